@@ -1,0 +1,246 @@
+"""Pins for oracle.extract_sg, oracle.prune, oracle.flow and oracle.verify."""
+from fractions import Fraction
+from itertools import combinations
+
+import numpy as np
+import pytest
+
+from oracle import brute, decomp, extract_sg, flow, fw, graph, prune, verify
+from helpers import load_expected, load_graph, frac, parse_ids, random_graph, random_planted
+from paper_2504_10937_gb300 import synth
+
+
+# ---------------------------------------------------------------- ExtractSG
+
+def test_cut_points_match_argmax_scan():
+    rng = synth.SplitMix64(5)
+    for _ in range(50):
+        nv = int(rng.integers(1, 25, 1)[0])
+        inc = rng.integers(0, 4, nv)
+        prefix = list(np.cumsum(inc))
+        want = []
+        for i in range(1, nv + 1):
+            dens = [Fraction(int(prefix[j - 1]), j) for j in range(i, nv + 1)]
+            best = max(dens)
+            j_star = max(j for j in range(i, nv + 1) if Fraction(int(prefix[j - 1]), j) == best)
+            if j_star == i:
+                want.append(i)
+        assert extract_sg.cut_points(prefix) == want
+
+
+def _ir_bounds(n, u, v):
+    core = graph.core_numbers(n, u, v)
+    return ({x: Fraction(int(core[x])) for x in range(n)},
+            {x: Fraction(int(core[x]), 2) for x in range(n)})
+
+
+def test_fig1_groups_near_optimum():
+    n, u, v = load_graph("fig1_graph.txt")
+    R, W, Dn, _ = fw.fw_edge_exact(n, u, v, 20000)
+    ub, lb = _ir_bounds(n, u, v)
+    res = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+    groups = [sorted(g) for g in res["groups"]]
+    assert groups == [list(range(6)), list(range(9, 14)), list(range(14, 18)), [6, 7, 8]]
+    exp = load_expected("fig1_expected.txt")
+    for (lo, hi), key in zip(res["intervals"], ["r_star_S1", "r_star_S2", "r_star_S3", "r_star_ghi"]):
+        assert lo <= frac(exp[key]) <= hi
+        assert hi - lo < Fraction(1, 100)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_bounds_contain_exact_phi(seed):
+    n, u, v, _ = random_planted(40, 0.08, (7, 6), (0.9, 0.7), seed=4000 + seed)
+    phi = decomp.compact_numbers(n, list(zip(u.tolist(), v.tolist())))
+    for N in (3, 20, 150):
+        R, W, Dn, _ = fw.fw_edge_exact(n, u, v, N)
+        ub, lb = _ir_bounds(n, u, v)
+        res = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+        for x in range(n):
+            assert res["lb"][x] <= phi[x] <= res["ub"][x]
+        # groups are consecutive blocks of the sorted order
+        flat = [x for g in res["groups"] for x in g] + res["remainder"]
+        assert flat == res["order"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_triangle_bounds_contain_exact_phi(seed):
+    n, u, v, _ = random_planted(30, 0.1, (7, 6), (0.9, 0.8), seed=5000 + seed)
+    tris = graph.triangles(n, u, v)
+    phi = decomp.compact_numbers(n, [tuple(t) for t in tris.tolist()])
+    core = graph.tr_core_numbers(n, tris)
+    for N in (3, 30, 200):
+        R, W, Dn3, _ = fw.fw_tri_exact(n, tris, N)
+        ub = {x: Fraction(int(core[x])) for x in range(n)}
+        lb = {x: Fraction(int(core[x]), 3) for x in range(n)}
+        res = extract_sg.extract_sg_tri(range(n), tris, W, Dn3, ub, lb)
+        for x in range(n):
+            assert res["lb"][x] <= phi[x] <= res["ub"][x]
+
+
+# ---------------------------------------------------------------- Pruning
+
+def test_fig1_pruning_example():
+    n, u, v = load_graph("fig1_graph.txt")
+    exp = load_expected("fig1_expected.txt")
+    phi = decomp.compact_numbers(n, list(zip(u.tolist(), v.tolist())))
+    groups = [list(range(6)), list(range(9, 14)), list(range(14, 18)), [6, 7, 8]]
+    kept, new_groups, r1, r2 = prune.prune(n, u, v, range(n), groups, phi, phi)
+    assert sorted(r1) == parse_ids(exp["pruned_rule1"])
+    assert sorted(r2) == parse_ids(exp["pruned_rule2"])
+    assert new_groups == [list(range(6)), list(range(9, 14))]
+
+
+@pytest.mark.parametrize("seed", range(15))
+def test_pruning_never_removes_lds_vertices(seed):
+    n, u, v = random_graph(10, 0.35, seed=6000 + seed)
+    lds_vertices = {x for _, c in brute.brute_lds(n, u, v) for x in c}
+    for N in (2, 10, 60):
+        R, W, Dn, _ = fw.fw_edge_exact(n, u, v, N)
+        ub, lb = _ir_bounds(n, u, v)
+        res = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+        kept, _, _, _ = prune.prune(n, u, v, range(n), res["groups"], res["ub"], res["lb"])
+        assert lds_vertices <= kept
+
+
+# ---------------------------------------------------------------- Flow
+
+@pytest.mark.parametrize("seed", range(20))
+def test_dinic_matches_brute_force_cut(seed):
+    rng = synth.SplitMix64(7000 + seed)
+    nn = 7
+    caps = {}
+    for a in range(nn):
+        for b in range(nn):
+            if a != b and rng.uniform(1)[0] < 0.4:
+                caps[(a, b)] = int(rng.integers(1, 9, 1)[0])
+    net = flow.FlowNetwork(nn)
+    for (a, b), c in caps.items():
+        net.add_edge(a, b, c)
+    value = net.max_flow(0, nn - 1)
+    best, best_sides = None, []
+    for mask in range(1 << nn):
+        if not mask & 1 or mask >> (nn - 1) & 1:
+            continue
+        cut = sum(c for (a, b), c in caps.items() if mask >> a & 1 and not mask >> b & 1)
+        if best is None or cut < best:
+            best, best_sides = cut, [mask]
+        elif cut == best:
+            best_sides.append(mask)
+    assert value == best
+    # maximal source side = union of all minimum source sides
+    union = 0
+    for m in best_sides:
+        union |= m
+    side = net.maximal_source_side(nn - 1)
+    assert sum(1 << x for x in side) == union
+
+
+# ---------------------------------------------------------------- Verification
+
+@pytest.mark.parametrize("seed", range(12))
+def test_is_densest_matches_enumeration(seed):
+    n, u, v = random_graph(9, 0.45, seed=8000 + seed)
+    en = brute.Enumeration(n, u, v)
+    adj = graph.adjacency(n, u, v)
+    for mask in range(1, 1 << n, 7):
+        S = [x for x in range(n) if mask >> x & 1]
+        eu, ev = graph.induced_edges(u, v, S)
+        want = en.densest_value(mask) == en.density(mask)
+        assert verify.is_densest(S, list(zip(eu.tolist(), ev.tolist()))) == want
+
+
+def _check_is_lds_against_definition(n, u, v, triangle, bounds):
+    en = brute.Enumeration(n, u, v, triangle)
+    truth = {tuple(c) for _, c in en.lds_list(include_zero=True)}
+    adj = graph.adjacency(n, u, v)
+    tris = graph.triangles(n, u, v)
+    tri_list = [tuple(t) for t in tris.tolist()]
+    tris_of = [[] for _ in range(n)]
+    for ti, t in enumerate(tri_list):
+        for w in t:
+            tris_of[w].append(ti)
+    ub, lb = bounds
+    checked = 0
+    for m, k in en.kappa.items():
+        if en.densest_value(m) != en.density(m):
+            continue            # verification assumes a self-densest candidate
+        S = [x for x in range(n) if m >> x & 1]
+        f = en.f[m]
+        if triangle:
+            got = verify.is_ltds(S, ub, lb, adj, tris_of, tri_list, f)
+        else:
+            got = verify.is_lds(S, ub, lb, adj, f)
+        assert got == (tuple(S) in truth), (S, got)
+        checked += 1
+    return checked
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("triangle", [False, True])
+def test_is_lds_with_exact_and_loose_bounds(seed, triangle):
+    n, u, v = random_graph(8, 0.4 + 0.05 * (seed % 3), seed=9000 + seed)
+    en = brute.Enumeration(n, u, v, triangle)
+    phi = en.compact_numbers()
+    exact = ({x: phi[x] for x in range(n)}, {x: phi[x] for x in range(n)})
+    _check_is_lds_against_definition(n, u, v, triangle, exact)
+    if triangle:
+        core = graph.tr_core_numbers(n, graph.triangles(n, u, v))
+        loose = ({x: Fraction(int(core[x])) for x in range(n)}, {x: Fraction(int(core[x]), 3) for x in range(n)})
+    else:
+        core = graph.core_numbers(n, u, v)
+        loose = ({x: Fraction(int(core[x])) for x in range(n)}, {x: Fraction(int(core[x]), 2) for x in range(n)})
+    _check_is_lds_against_definition(n, u, v, triangle, loose)
+
+
+def test_direct_denser_neighbour_rejects():
+    # K_20 joined by one edge to K_40: K_20 minus the bridge vertex is self-densest,
+    # has phi = 191/20 on all of K_20, and is not an LDS (its neighbour b0 is denser)
+    a = list(combinations(range(40), 2))
+    b = list(combinations(range(40, 60), 2))
+    pairs = a + b + [(0, 40)]
+    n = 60
+    u, v = map(np.array, zip(*pairs))
+    phi = decomp.compact_numbers(n, pairs)
+    assert phi[41] == Fraction(191, 20)
+    S = list(range(41, 60))
+    adj = graph.adjacency(n, u, v)
+    assert not verify.is_lds(S, phi, phi, adj, 171)
+    assert verify.is_lds(list(range(40)), phi, phi, adj, 780)
+
+
+@pytest.mark.parametrize("triangle", [False, True])
+def test_lds_never_meets_two_accepted_groups(triangle):
+    # the driver's completeness rests on this (see oracle.ldscvx); checked here on
+    # random and planted graphs at small and moderate iteration counts
+    checks = 0
+    for seed in range(40):
+        if seed % 2:
+            n, u, v = random_graph(10, 0.35 + 0.05 * (seed % 5), seed=30000 + seed)
+            truth = brute.brute_lds(n, u, v, triangle=triangle)
+        else:
+            n, u, v, _ = random_planted(36, 0.07, (7, 6, 5), (0.9, 0.8, 0.9), seed=30000 + seed)
+            if triangle:
+                truth = decomp.ltds_exact(n, u, v, graph.triangles(n, u, v))
+            else:
+                truth = decomp.lds_exact(n, u, v)
+        if triangle:
+            tris = graph.triangles(n, u, v)
+            core = graph.tr_core_numbers(n, tris)
+            div = 3
+        else:
+            core = graph.core_numbers(n, u, v)
+            div = 2
+        for N in (1, 3, 10, 40):
+            ub = {x: Fraction(int(core[x])) for x in range(n)}
+            lb = {x: Fraction(int(core[x]), div) for x in range(n)}
+            if triangle:
+                R, W, Dn, _ = fw.fw_tri_exact(n, tris, N)
+                res = extract_sg.extract_sg_tri(range(n), tris, W, Dn, ub, lb)
+            else:
+                R, W, Dn, _ = fw.fw_edge_exact(n, u, v, N)
+                res = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+            groups = [set(gr) for gr in res["groups"]] + ([set(res["remainder"])] if res["remainder"] else [])
+            for _, T in truth:
+                assert sum(1 for gr in groups if gr & set(T)) == 1
+                checks += 1
+    assert checks > 100
