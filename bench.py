@@ -1,0 +1,304 @@
+"""Benchmark: Frank-Wolfe edge-updates per second on the power-law workload.
+
+Workload: Chung-Lu graph with n = 1,000,000 vertices, 10,000,000 background
+edges (degree exponent 2.1) plus 50 planted blocks of log-uniform size 50-500
+and edge probability U(0.3, 0.9) (about 10.8M edges in all), delivered as a raw
+edge list (random orientation and order, 5% repeated pairs, 1% self-loops)
+already resident in device memory.
+
+One step = one pass of the path on that input: graph ingest (canonical edges +
+CSR) followed by 500 Frank-Wolfe iterations (Alg. 1) in the chosen
+arithmetic.  value = edge-updates (m * iterations) / step time.  L2 is flushed
+between steps (a 512 MiB device write outside the per-step events).
+
+``--impl reference`` times the CPU oracle (oracle.fw) on the host cores on a
+bounded number of iterations of the same graph and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2504_10937_gb300 import synth  # noqa: E402
+
+METRIC = "FW edge-updates/s"
+UNIT = "edge-updates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(args):
+    n, u, v, blocks = synth.workload_chung_lu_1m(seed=2)
+    a, b = synth.scramble(n, u, v, seed=20)
+    return n, u, v, a, b
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores (bounded sample)."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import fw as ofw
+    n, u, v, a, b = _workload(args)
+    u64 = u.astype(np.int64)
+    v64 = v.astype(np.int64)
+    m = len(u)
+    iters_per_step = args.ref_iters
+    times = []
+    R, W = None, None
+    i = 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        R, W, _, _ = ofw.fw_edge_exact(n, u64, v64, i + iters_per_step, R0=R, W0=W, i0=i)
+        dt = time.perf_counter() - t0
+        i += iters_per_step
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = m * iters_per_step * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": _config(args, n, m),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{iters_per_step} exact FW iterations per step on the full graph (m={m})"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, n, m):
+    return {"workload": "chung_lu_n1e6_m1e7_exp2.1_50blocks (seed 2), raw COO with 5% repeats and 1% self-loops",
+            "n": n, "m": m, "iters": args.iters, "precision": args.precision, "density": "edge",
+            "step": "ingest + Frank-Wolfe", "l2": "flushed between steps (512 MiB device write)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def cpu_baseline(n, u, v, budget_s=12.0):
+    from oracle import fw as ofw
+    u64 = u.astype(np.int64)
+    v64 = v.astype(np.int64)
+    t0 = time.perf_counter()
+    R, W, _, _ = ofw.fw_edge_exact(n, u64, v64, 1)
+    one = time.perf_counter() - t0
+    iters = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    ofw.fw_edge_exact(n, u64, v64, 1 + iters, R0=R, W0=W, i0=1)
+    dt = time.perf_counter() - t0
+    return {"value": len(u) * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} exact FW iterations (iterations 2..{iters + 1}) of the oracle on the full graph"}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2504_10937_gb300 import lds
+    lds.load()
+    n, u, v, a, b = _workload(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ta = torch.from_numpy(a).to(dev)
+    tb = torch.from_numpy(b).to(dev)
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    m_holder = {}
+
+    def step():
+        g = lds.Graph(n, ta, tb, stream=sptr)
+        m_holder["m"] = g.m
+        g.fw(args.iters, precision=args.precision, want=())
+        t = g.fw_timing()
+        g.close()
+        return t
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    lds.set_pass_profiling(True)
+    times, pass_us, fw_ms = [], [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = lds.launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            pass_us.append(t["pass_us"])
+            fw_ms.append(t["fw_ms"])
+            flush.zero_()
+        torch.cuda.synchronize()
+    launches = lds.launch_count() - launches0
+    lds.set_pass_profiling(False)
+    if world > 1:
+        torch.distributed.barrier()
+    m = m_holder["m"]
+    total_ms = sum(times)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    units = m * args.iters * args.steps * world
+    value = units / (total_ms / 1000.0)
+
+    # end to end through the C-ABI with host (pinned) buffers
+    ha = torch.from_numpy(a).pin_memory()
+    hb = torch.from_numpy(b).pin_memory()
+    e2e_times = []
+    for k in range(0 if args.no_e2e else max(2, args.steps // 2) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = lds.Graph(n, ha.numpy(), hb.numpy(), stream=sptr)
+        out = g.fw(args.iters, precision=args.precision, want=("r",))
+        g.close()
+        dt = time.perf_counter() - t0
+        if k:
+            e2e_times.append(dt)
+        flush.zero_()
+    e2e_value = m * args.iters / statistics.mean(e2e_times) if e2e_times else None
+
+    hbm, peak_kind = _peaks()
+    nslots = 2 * m
+    nchunks = (nslots + 31) // 32
+    bytes_per_pass = 4 * nslots + 8 * nchunks + 8 * n
+    avg_pass_us = statistics.mean(pass_us)
+    achieved = bytes_per_pass / (avg_pass_us * 1e-6) / 1e9
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"exact": "int64", "fp32": "f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": _config(args, n, m),
+            "fw_only": {"value": m * args.iters / (statistics.mean(fw_ms) / 1000.0), "unit": UNIT,
+                        "fw_ms": statistics.mean(fw_ms)},
+            "roofline": {"bound": "hbm", "kernel": "fw_edge_pass_kernel", "achieved": achieved, "peak": hbm,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_us": avg_pass_us},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * len(a)),
+                    "d2h_bytes_per_step": int(8 * n)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(n, u, v)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=500)
+    ap.add_argument("--precision", choices=["exact", "fp32", "fp64"], default="exact")
+    ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * liblds - top-k locally densest subgraphs (LDS, edge density) and locally
+ * triangle-densest subgraphs (LTDS) on one NVIDIA GB300 (sm_103a), following
+ * arXiv 2504.10937, "Finding Locally Densest Subgraphs: Convex Programming with
+ * Edge and Triangle Density".
+ *
+ * Conventions for every entry point
+ *   - Vertex ids are int32 in [0, n), n <= 2^31 - 2.  The graph is simple and
+ *     undirected; input pairs may repeat, appear in either orientation or be
+ *     self-loops: repeats and self-loops are dropped at ingest (Sec. 3).
+ *   - "Canonical edge order" is the list of distinct pairs (u, v), u < v,
+ *     sorted by (u, v).  "Triangle order" lists every triangle {a < b < c}
+ *     sorted by (a, b, c).  Every per-edge / per-triangle array in and out of
+ *     the library uses these orders and original vertex ids.
+ *   - Buffers are host or device memory as the lds_mem argument says; the
+ *     caller owns every buffer it passes, and the library keeps no pointer to
+ *     them after the call returns.
+ *   - Calls enqueue work on the graph's stream (set at creation, NULL = the
+ *     legacy default stream) and return when results are visible to the
+ *     caller.  A handle must not be used from two threads at once; different
+ *     handles are independent.
+ *   - No call throws.  Each returns an lds_status; on failure lds_last_error()
+ *     gives a thread-local message and output buffers are unspecified.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns LDS_ECUDA.
+ */
+#ifndef LDS_H
+#define LDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDS_OK = 0,
+    LDS_EINVAL = 1,     /* bad argument: id out of range, null pointer, size  */
+    LDS_ENOMEM = 2,     /* device or host allocation failed                   */
+    LDS_ECUDA = 3,      /* CUDA runtime error or no device                    */
+    LDS_ETIMEOUT = 4,   /* a bounded device loop hit its iteration cap        */
+    LDS_EOVERFLOW = 5,  /* a value does not fit the integer range used        */
+    LDS_EBUSY = 6       /* request refused: over the memory budget            */
+} lds_status;
+
+typedef enum { LDS_EDGE = 0, LDS_TRIANGLE = 1 } lds_density;
+
+/* Arithmetic of the Frank-Wolfe iterations (Alg. 1 / Alg. 6).
+ *   LDS_EXACT: integer form.  With D_i = (i+1)(i+2), W = D_i alpha and
+ *              R = D_i r are integers (3 D_i for triangles); bit-exact.
+ *   LDS_FP32:  loads carried in binary32 by r <- (1-gamma) r + gamma c (the sum
+ *              of Alg. 1's alpha update over a vertex's edges); the weights are
+ *              rebuilt exactly from the choices made.
+ *   LDS_FP64:  Alg. 1 / Alg. 6 literally in binary64: one alpha per ordered
+ *              pair (vertex-triangle pair), r summed per vertex in ascending
+ *              neighbour (triangle) order.  The plain reference path.        */
+typedef enum { LDS_EXACT = 0, LDS_FP64 = 1, LDS_FP32 = 2 } lds_precision;
+
+typedef enum { LDS_MEM_HOST = 0, LDS_MEM_DEVICE = 1 } lds_mem;
+
+typedef struct lds_graph lds_graph;
+
+typedef struct {
+    int32_t n;                 /* vertices                                    */
+    int64_t m;                 /* distinct undirected edges                   */
+    int64_t input_pairs;       /* pairs passed to lds_create_graph            */
+    int64_t self_loops;        /* of which self-loops (dropped)               */
+    int64_t duplicates;        /* of which repeats of an earlier pair         */
+    int32_t max_degree;
+    int32_t isolated;          /* vertices without an edge                    */
+    int64_t triangles;         /* |T| once listed (lds_list_triangles), else -1 */
+} lds_graph_info_t;
+
+/* Library version string. */
+const char* lds_version(void);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* lds_last_error(void);
+
+/* Number of CUDA devices visible (0 when none); never fails. */
+int32_t lds_device_count(void);
+
+/* Graph ingest (Sec. 3: G = (V, E) simple and undirected).
+ *   n          number of vertices
+ *   m          number of input pairs (src[i], dst[i])
+ *   src, dst   int32[m] in host or device memory per `where`; copied
+ *   stream     cudaStream_t for all work on this graph (NULL: default stream)
+ *   out        receives the new handle; free with lds_free
+ * Builds the canonical edge list and a symmetric CSR on the device.
+ * Errors: LDS_EINVAL (n < 0, m < 0, null pointers, id outside [0, n)),
+ *         LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_create_graph(int32_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            lds_mem where, void* stream, lds_graph** out);
+
+/* Releases every device buffer of the handle (NULL is ignored). */
+void lds_free(lds_graph* g);
+
+lds_status lds_graph_info(const lds_graph* g, lds_graph_info_t* info);
+
+/* Canonical edges: u[e] < v[e], int32[m] each, sorted by (u, v). */
+lds_status lds_get_edges(const lds_graph* g, int32_t* u, int32_t* v, lds_mem where);
+
+/* Triangle listing (the set T of Eq. 3 / Eq. 4, needed by Alg. 6 and Alg. 7).
+ * Lists T once and keeps it on the device with the handle; writes |T|.
+ * Errors: LDS_ENOMEM when T does not fit, LDS_ECUDA. */
+lds_status lds_list_triangles(lds_graph* g, int64_t* count);
+
+/* Copies T (after lds_list_triangles) as int32[3 |T|] rows (a, b, c), a < b < c,
+ * in triangle order. */
+lds_status lds_get_triangles(lds_graph* g, int32_t* tri, lds_mem where);
+
+/* Core numbers (Def. 6) or tr-core numbers (Def. 11) of every vertex: int64[n].
+ * LDS_TRIANGLE lists triangles first if needed. */
+lds_status lds_core_numbers(lds_graph* g, lds_density d, int64_t* core, lds_mem where);
+
+/* Results of lds_fw; every pointer may be NULL to skip that output.        */
+typedef struct {
+    double*  r;        /* [n] loads r_u after `iters` iterations: EXACT gives R_u / D
+                          rounded once, FP32 the binary32 value, FP64 the binary64 value */
+    int64_t* R;        /* [n] exact scaled loads of the returned weights: R_u = D r_u   */
+    int64_t* W;        /* [m] D alpha_{u,v} per canonical edge (edge density), or
+                          [3 |T|] D alpha_{w,t} per triangle row (triangle density)     */
+    uint8_t* last;     /* [m] alpha_hat_{u,v} of the last iteration (1: u received), or
+                          [|T|] column (0, 1, 2) of the triangle's receiving vertex     */
+    int64_t  D;        /* out: denominator, (N+1)(N+2) (edges) or 3(N+1)(N+2)           */
+} lds_fw_result;
+
+/* Frank-Wolfe for CP(G) (Eq. 2, Alg. 1) or for the triangle program (Eq. 4,
+ * Alg. 6) from the initial point alpha = 1/2 (1/3), `iters` iterations.
+ * Ties: an edge (u, v), u < v, goes to u only when r_u < r_v (Alg. 1), so ties
+ * go to the larger id; a triangle goes to its lowest-load vertex, ties to the
+ * larger id (appendix, proof of Thm. 4).
+ *   where   memory kind of every output pointer in `out`
+ * Errors: LDS_EINVAL (iters < 0, iters > 60000, bad precision),
+ *         LDS_EOVERFLOW (scaled loads exceed int64), LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, lds_mem where,
+                  lds_fw_result* out);
+
+/* Times of the most recent lds_fw call on this handle, measured with CUDA events
+ * on the handle's stream: total FW milliseconds and the average duration of the
+ * dominant per-iteration kernel (the edge or triangle pass) in microseconds. */
+lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us,
+                              int64_t* pass_launches);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (process-wide counter; never fails). */
+int64_t lds_launch_count(void);
+
+/* When on != 0, lds_fw records a CUDA event pair around every pass launch so
+ * that lds_fw_last_timing can report the pass kernel's average duration. */
+void lds_set_pass_profiling(int32_t on);
+
+/* Test hook: make the k-th device allocation from now fail with LDS_ENOMEM
+ * (k <= 0 disables).  Host-side fault injection; no GPU fault involved. */
+void lds_debug_fail_alloc_after(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDS_H */

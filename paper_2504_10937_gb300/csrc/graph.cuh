@@ -1,0 +1,52 @@
+// The graph handle and its device layout.
+//
+// Internal ids: the non-isolated vertices keep their relative order and are
+// numbered 0..nact-1; isolated vertices follow.  The map is monotone on
+// non-isolated vertices, so comparisons by id (the FW tie rule, the (u, v)
+// order of edges, the (a, b, c) order of triangles) are the same in internal
+// and original ids, and every row 0..nact-1 of the CSR is non-empty.
+#pragma once
+
+#include "common.cuh"
+
+struct lds_graph {
+    int32_t n = 0;        // vertices (original id space)
+    int32_t nact = 0;     // non-isolated vertices (internal ids 0..nact-1)
+    int64_t m = 0;        // distinct undirected edges
+    cudaStream_t stream = nullptr;
+    lds_graph_info_t info{};
+
+    lds::DevBuf<int32_t> to_orig;     // [n] internal -> original
+    lds::DevBuf<int32_t> to_int;      // [n] original -> internal
+    lds::DevBuf<int32_t> eu, ev;      // [m] canonical edges, internal ids, u < v
+    lds::DevBuf<int64_t> rowptr;      // [nact + 1]
+    lds::DevBuf<int32_t> col;         // [2m] internal ids, ascending in each row
+    lds::DevBuf<int32_t> fwcol;       // [2m] col with bit 31 set on the first slot of each row
+    lds::DevBuf<int32_t> chunk_row0;  // [ceil(2m / 32)] row of slot 32 g
+    lds::DevBuf<int64_t> slot_edge;   // [2m] canonical edge id of each slot (lazy)
+
+    // triangles (lazy): internal ids a < b < c, triangle order
+    int64_t ntri = -1;
+    lds::DevBuf<int32_t> ta, tb, tc;
+
+    // timing of the most recent lds_fw
+    double fw_ms = 0.0, pass_us = 0.0;
+    int64_t pass_launches = 0;
+};
+
+namespace lds {
+
+// Builds slot_edge (canonical edge id of every CSR slot) if not present.
+void ensure_slot_edge(lds_graph* g);
+
+// Lists triangles into g->ta/tb/tc if not present.
+void ensure_triangles(lds_graph* g);
+
+// out[i] = map[in[i]] for i < k.
+void map_ids(const int32_t* in, const int32_t* map, int64_t k, int32_t* out, cudaStream_t s);
+
+// Scatter a per-internal-vertex array to original ids: out[to_orig[i]] = in[i].
+void to_original_order_i64(const lds_graph* g, const int64_t* in_int, int64_t* out_orig);
+void to_original_order_f64(const lds_graph* g, const double* in_int, double* out_orig);
+
+}  // namespace lds

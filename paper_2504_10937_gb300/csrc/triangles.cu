@@ -1,0 +1,380 @@
+// Triangle listing (the set T of Eq. 3 / Eq. 4) and core / tr-core numbers
+// (Def. 6, Def. 11).
+//
+// Listing: every edge is oriented from the endpoint of lower (degree, id) rank
+// to the higher one, which bounds out-degrees by O(sqrt(m)); each oriented edge
+// x -> y meets out(x) and out(y) (both ascending) by a merge walk, and each
+// common out-neighbour w closes the triangle {x, y, w} exactly once.  A count
+// pass sizes the output, a write pass fills it, and two stable radix sorts put
+// the rows in (a, b, c) order.
+//
+// Core numbers: level-synchronous peeling.  At level k every live vertex whose
+// remaining degree (number of live triangles for tr-core) is <= k gets core k
+// and is removed, its neighbours' degrees drop, and the step repeats until no
+// vertex is removed; then k moves to the smallest remaining degree.
+#include <algorithm>
+
+#include "graph.cuh"
+#include "prims.cuh"
+
+namespace lds {
+
+namespace {
+
+__device__ __forceinline__ bool precedes(int32_t dx, int32_t x, int32_t dy, int32_t y) {
+    return dx < dy || (dx == dy && x < y);
+}
+
+__global__ void orient_count_kernel(const int64_t* rowptr, const int32_t* col, int32_t nact, int32_t* outdeg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
+        int64_t b = rowptr[x], e = rowptr[x + 1];
+        int32_t dx = (int32_t)(e - b);
+        int32_t c = 0;
+        for (int64_t s = b; s < e; ++s) {
+            int32_t y = col[s];
+            int32_t dy = (int32_t)(rowptr[y + 1] - rowptr[y]);
+            c += precedes(dx, (int32_t)x, dy, y);
+        }
+        outdeg[x] = c;
+    }
+}
+
+__global__ void orient_fill_kernel(const int64_t* rowptr, const int32_t* col, int32_t nact, const int64_t* optr,
+                                   int32_t* ocol) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
+        int64_t b = rowptr[x], e = rowptr[x + 1];
+        int32_t dx = (int32_t)(e - b);
+        int64_t o = optr[x];
+        for (int64_t s = b; s < e; ++s) {
+            int32_t y = col[s];
+            int32_t dy = (int32_t)(rowptr[y + 1] - rowptr[y]);
+            if (precedes(dx, (int32_t)x, dy, y)) ocol[o++] = y;
+        }
+    }
+}
+
+// source vertex of every oriented slot
+__global__ void oriented_src_kernel(const int64_t* optr, int32_t nact, int32_t* osrc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
+        for (int64_t s = optr[x], e = optr[x + 1]; s < e; ++s) osrc[s] = (int32_t)x;
+}
+
+template <bool WRITE>
+__global__ void tri_intersect_kernel(const int64_t* optr, const int32_t* ocol, const int32_t* osrc, int64_t nos,
+                                     int64_t* count, const int64_t* offset, int32_t* ta, int32_t* tb, int32_t* tc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nos; s += stride) {
+        int32_t x = osrc[s], y = ocol[s];
+        int64_t i = optr[x], ie = optr[x + 1];
+        int64_t j = optr[y], je = optr[y + 1];
+        int64_t c = 0;
+        int64_t o = WRITE ? offset[s] : 0;
+        while (i < ie && j < je) {
+            int32_t a = ocol[i], b = ocol[j];
+            if (a < b) ++i;
+            else if (b < a) ++j;
+            else {
+                if (WRITE) {
+                    int32_t p = x, q = y, r = a;
+                    if (p > q) { int32_t t = p; p = q; q = t; }
+                    if (q > r) { int32_t t = q; q = r; r = t; }
+                    if (p > q) { int32_t t = p; p = q; q = t; }
+                    ta[o] = p; tb[o] = q; tc[o] = r;
+                    ++o;
+                }
+                ++c; ++i; ++j;
+            }
+        }
+        if (!WRITE) count[s] = c;
+    }
+}
+
+__global__ void tri_key_bc_kernel(const int32_t* tb, const int32_t* tc, int64_t ntri, int64_t nn, uint64_t* key,
+                                  uint32_t* idx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        key[t] = (uint64_t)tb[t] * (uint64_t)nn + (uint64_t)tc[t];
+        idx[t] = (uint32_t)t;
+    }
+}
+
+__global__ void tri_key_a_kernel(const int32_t* ta, const uint32_t* idx, int64_t ntri, uint64_t* key) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) key[t] = (uint64_t)ta[idx[t]];
+}
+
+__global__ void permute3_kernel(const int32_t* a, const int32_t* b, const int32_t* c, const uint32_t* idx, int64_t k,
+                                int32_t* oa, int32_t* ob, int32_t* oc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < k; t += stride) {
+        uint32_t j = idx[t];
+        oa[t] = a[j]; ob[t] = b[j]; oc[t] = c[j];
+    }
+}
+
+__global__ void tri_rows_orig_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, const int32_t* to_orig,
+                                     int64_t ntri, int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        out[3 * t] = to_orig[ta[t]];
+        out[3 * t + 1] = to_orig[tb[t]];
+        out[3 * t + 2] = to_orig[tc[t]];
+    }
+}
+
+// ---- peeling
+
+__global__ void peel_select_kernel(const int32_t* deg, uint8_t* alive, int32_t nact, int64_t k, int64_t* core,
+                                   int32_t* frontier, int32_t* fcount, int64_t* min_alive) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
+        if (!alive[x]) continue;
+        if (deg[x] <= k) {
+            alive[x] = 0;
+            core[x] = k;
+            frontier[atomicAdd(fcount, 1)] = (int32_t)x;
+        } else {
+            atomicMin((unsigned long long*)min_alive, (unsigned long long)deg[x]);
+        }
+    }
+}
+
+__global__ void peel_edges_kernel(const int64_t* rowptr, const int32_t* col, const int32_t* frontier, int32_t fcount,
+                                  const uint8_t* alive, int32_t* deg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += stride) {
+        int32_t x = frontier[i];
+        for (int64_t s = rowptr[x], e = rowptr[x + 1]; s < e; ++s) {
+            int32_t y = col[s];
+            if (alive[y]) atomicSub(deg + y, 1);
+        }
+    }
+}
+
+__global__ void peel_tris_kernel(const int64_t* vptr, const int32_t* vtri, const int32_t* frontier, int32_t fcount,
+                                 const int32_t* ta, const int32_t* tb, const int32_t* tc, uint8_t* tdead,
+                                 const uint8_t* alive, int32_t* deg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += stride) {
+        int32_t x = frontier[i];
+        for (int64_t s = vptr[x], e = vptr[x + 1]; s < e; ++s) {
+            int32_t t = vtri[s];
+            unsigned int* word = (unsigned int*)(tdead + (t & ~3));
+            unsigned int bit = 1u << (8 * (t & 3));
+            unsigned int old = atomicOr(word, bit);
+            if (old & bit) continue;
+            int32_t a = ta[t], b = tb[t], c = tc[t];
+            if (a != x && alive[a]) atomicSub(deg + a, 1);
+            if (b != x && alive[b]) atomicSub(deg + b, 1);
+            if (c != x && alive[c]) atomicSub(deg + c, 1);
+        }
+    }
+}
+
+__global__ void degree_kernel(const int64_t* rowptr, int32_t nact, int32_t* deg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
+        deg[x] = (int32_t)(rowptr[x + 1] - rowptr[x]);
+}
+
+__global__ void vt_count_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        atomicAdd(cnt + ta[t], 1);
+        atomicAdd(cnt + tb[t], 1);
+        atomicAdd(cnt + tc[t], 1);
+    }
+}
+
+__global__ void vt_fill_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
+                               const int64_t* vptr, int32_t* cursor, int32_t* vtri) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        int32_t v3[3] = {ta[t], tb[t], tc[t]};
+        for (int k = 0; k < 3; ++k) vtri[vptr[v3[k]] + atomicAdd(cursor + v3[k], 1)] = (int32_t)t;
+    }
+}
+
+__global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < to; x += stride) p[x] = v;
+}
+
+}  // namespace
+
+void ensure_triangles(lds_graph* g) {
+    if (g->ntri >= 0) return;
+    cudaStream_t s = g->stream;
+    const int32_t nact = g->nact;
+    const int blk = 256;
+    if (g->m == 0 || nact == 0) {
+        g->ntri = 0;
+        return;
+    }
+    DevBuf<int32_t> outdeg(nact + 1, s);
+    LDS_CUDA(cudaMemsetAsync(outdeg.get(), 0, (nact + 1) * sizeof(int32_t), s));
+    LDS_LAUNCH(orient_count_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), g->col.get(), nact, outdeg.get());
+    LDS_CHECK_LAUNCH();
+    DevBuf<int64_t> optr(nact + 1, s);
+    int64_t nos = exclusive_scan_i32_to_i64(outdeg.get(), optr.get(), nact + 1, s);
+    LDS_REQUIRE(nos == g->m, LDS_ECUDA, "triangle listing: orientation lost edges (internal error)");
+    DevBuf<int32_t> ocol(nos, s), osrc(nos, s);
+    LDS_LAUNCH(orient_fill_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), g->col.get(), nact, optr.get(), ocol.get());
+    LDS_LAUNCH(oriented_src_kernel, grid_for(nact, blk), blk, 0, s, optr.get(), nact, osrc.get());
+    LDS_CHECK_LAUNCH();
+    DevBuf<int64_t> cnt(nos, s), off(nos, s);
+    LDS_LAUNCH(tri_intersect_kernel<false>, grid_for(nos, blk), blk, 0, s, optr.get(), ocol.get(), osrc.get(), nos, cnt.get(),
+                                                                   nullptr, nullptr, nullptr, nullptr);
+    LDS_CHECK_LAUNCH();
+    int64_t ntri = exclusive_scan_i64(cnt.get(), off.get(), nos, s);
+    LDS_REQUIRE(ntri < ((int64_t)1 << 32), LDS_EOVERFLOW, "triangle listing: |T| = %lld exceeds 2^32",
+                (long long)ntri);
+    DevBuf<int32_t> a(ntri, s), b(ntri, s), c(ntri, s);
+    if (ntri) {
+        LDS_LAUNCH(tri_intersect_kernel<true>, grid_for(nos, blk), blk, 0, s, optr.get(), ocol.get(), osrc.get(), nos, nullptr,
+                                                                      off.get(), a.get(), b.get(), c.get());
+        LDS_CHECK_LAUNCH();
+    }
+    cnt.release(); off.release(); ocol.release(); osrc.release(); optr.release(); outdeg.release();
+    g->ta.alloc(ntri, s);
+    g->tb.alloc(ntri, s);
+    g->tc.alloc(ntri, s);
+    if (ntri) {
+        DevBuf<uint64_t> key(ntri, s);
+        DevBuf<uint32_t> idx(ntri, s);
+        const uint64_t nn = (uint64_t)nact;
+        LDS_LAUNCH(tri_key_bc_kernel, grid_for(ntri, blk), blk, 0, s, b.get(), c.get(), ntri, (int64_t)nn, key.get(), idx.get());
+        LDS_CHECK_LAUNCH();
+        radix_sort_u64(key.get(), idx.get(), ntri, bit_length_u64(nn * nn), s);
+        LDS_LAUNCH(tri_key_a_kernel, grid_for(ntri, blk), blk, 0, s, a.get(), idx.get(), ntri, key.get());
+        LDS_CHECK_LAUNCH();
+        radix_sort_u64(key.get(), idx.get(), ntri, bit_length_u64(nn), s);
+        LDS_LAUNCH(permute3_kernel, grid_for(ntri, blk), blk, 0, s, a.get(), b.get(), c.get(), idx.get(), ntri, g->ta.get(),
+                                                            g->tb.get(), g->tc.get());
+        LDS_CHECK_LAUNCH();
+    }
+    LDS_CUDA(cudaStreamSynchronize(s));
+    g->ntri = ntri;
+    g->info.triangles = ntri;
+}
+
+// core numbers in internal ids: core_int[nact]
+static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int) {
+    cudaStream_t s = g->stream;
+    const int32_t nact = g->nact;
+    const int blk = 256;
+    if (nact == 0) return;
+    DevBuf<int32_t> deg(nact, s), frontier(nact, s), fcount(1, s);
+    DevBuf<uint8_t> alive(nact, s);
+    DevBuf<int64_t> minalive(1, s);
+    LDS_CUDA(cudaMemsetAsync(alive.get(), 1, nact, s));
+    DevBuf<int64_t> vptr;
+    DevBuf<int32_t> vtri;
+    DevBuf<uint8_t> tdead;
+    if (!tri) {
+        LDS_LAUNCH(degree_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), nact, deg.get());
+        LDS_CHECK_LAUNCH();
+    } else {
+        ensure_triangles(g);
+        const int64_t ntri = g->ntri;
+        LDS_CUDA(cudaMemsetAsync(deg.get(), 0, nact * sizeof(int32_t), s));
+        if (ntri) LDS_LAUNCH(vt_count_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri, deg.get());
+        LDS_CHECK_LAUNCH();
+        vptr.alloc(nact + 1, s);
+        DevBuf<int32_t> deg1(nact + 1, s);
+        LDS_CUDA(cudaMemsetAsync(deg1.get(), 0, (nact + 1) * sizeof(int32_t), s));
+        LDS_CUDA(cudaMemcpyAsync(deg1.get(), deg.get(), nact * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        exclusive_scan_i32_to_i64(deg1.get(), vptr.get(), nact + 1, s);
+        vtri.alloc(std::max<int64_t>(3 * ntri, 1), s);
+        DevBuf<int32_t> cursor(nact, s);
+        LDS_CUDA(cudaMemsetAsync(cursor.get(), 0, nact * sizeof(int32_t), s));
+        if (ntri) LDS_LAUNCH(vt_fill_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri, vptr.get(),
+                                                                     cursor.get(), vtri.get());
+        LDS_CHECK_LAUNCH();
+        tdead.alloc(((ntri + 3) & ~3ll) + 4, s);
+        LDS_CUDA(cudaMemsetAsync(tdead.get(), 0, ((ntri + 3) & ~3ll) + 4, s));
+    }
+    int64_t k = 0;
+    int32_t remaining = nact;
+    int64_t guard_steps = 0;
+    while (remaining > 0) {
+        LDS_CUDA(cudaMemsetAsync(fcount.get(), 0, sizeof(int32_t), s));
+        int64_t big = INT64_MAX;
+        LDS_CUDA(cudaMemcpyAsync(minalive.get(), &big, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        LDS_LAUNCH(peel_select_kernel, grid_for(nact, blk), blk, 0, s, deg.get(), alive.get(), nact, k, core_int, frontier.get(),
+                                                               fcount.get(), minalive.get());
+        LDS_CHECK_LAUNCH();
+        int32_t hf = 0;
+        int64_t hmin = 0;
+        LDS_CUDA(cudaMemcpyAsync(&hf, fcount.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaMemcpyAsync(&hmin, minalive.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        if (hf == 0) {
+            // nothing at this level: jump to the smallest live degree
+            k = std::max<int64_t>(k + 1, hmin);
+            continue;
+        }
+        remaining -= hf;
+        if (!tri)
+            LDS_LAUNCH(peel_edges_kernel, grid_for(hf, 128), 128, 0, s, g->rowptr.get(), g->col.get(), frontier.get(), hf,
+                                                                alive.get(), deg.get());
+        else
+            LDS_LAUNCH(peel_tris_kernel, grid_for(hf, 128), 128, 0, s, vptr.get(), vtri.get(), frontier.get(), hf, g->ta.get(),
+                                                               g->tb.get(), g->tc.get(), tdead.get(), alive.get(),
+                                                               deg.get());
+        LDS_CHECK_LAUNCH();
+        LDS_REQUIRE(++guard_steps < 4 * (int64_t)nact + 16, LDS_ETIMEOUT, "core numbers: peeling did not finish");
+    }
+}
+
+void core_numbers(lds_graph* g, bool tri, int64_t* core_int_out) { core_numbers_internal(g, tri, core_int_out); }
+
+}  // namespace lds
+
+using namespace lds;
+
+extern "C" {
+
+lds_status lds_list_triangles(lds_graph* g, int64_t* count) {
+    return guard([&] {
+        LDS_REQUIRE(g, LDS_EINVAL, "lds_list_triangles: NULL graph");
+        ensure_triangles(g);
+        if (count) *count = g->ntri;
+    });
+}
+
+lds_status lds_get_triangles(lds_graph* g, int32_t* tri, lds_mem where) {
+    return guard([&] {
+        LDS_REQUIRE(g && tri, LDS_EINVAL, "lds_get_triangles: NULL argument");
+        LDS_REQUIRE(g->ntri >= 0, LDS_EINVAL, "lds_get_triangles: call lds_list_triangles first");
+        if (g->ntri == 0) return;
+        cudaStream_t s = g->stream;
+        DevBuf<int32_t> rows(3 * g->ntri, s);
+        LDS_LAUNCH(tri_rows_orig_kernel, grid_for(g->ntri, 256), 256, 0, s, g->ta.get(), g->tb.get(), g->tc.get(),
+                                                                    g->to_orig.get(), g->ntri, rows.get());
+        LDS_CHECK_LAUNCH();
+        copy_out(tri, where, rows.get(), 3 * g->ntri * sizeof(int32_t), s);
+        LDS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+lds_status lds_core_numbers(lds_graph* g, lds_density d, int64_t* core, lds_mem where) {
+    return guard([&] {
+        LDS_REQUIRE(g && core, LDS_EINVAL, "lds_core_numbers: NULL argument");
+        LDS_REQUIRE(d == LDS_EDGE || d == LDS_TRIANGLE, LDS_EINVAL, "lds_core_numbers: bad density");
+        cudaStream_t s = g->stream;
+        const int32_t n = g->n;
+        if (n == 0) return;
+        DevBuf<int64_t> ci(n, s), co(n, s);
+        LDS_CUDA(cudaMemsetAsync(ci.get(), 0, n * sizeof(int64_t), s));
+        core_numbers_internal(g, d == LDS_TRIANGLE, ci.get());
+        to_original_order_i64(g, ci.get(), co.get());
+        copy_out(core, where, co.get(), n * sizeof(int64_t), s);
+        LDS_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+}  // extern "C"

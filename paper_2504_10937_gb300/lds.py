@@ -1,0 +1,222 @@
+"""Python binding of liblds (argument marshalling only).
+
+Every function calls the C-ABI declared in ``include/lds.h``; no step of the
+method runs in Python.  Host inputs are numpy arrays; device inputs are torch
+CUDA tensors (their data pointers are passed through).  Outputs come back as
+numpy arrays unless a device output is requested.  If ``liblds.so`` has not been
+built, :func:`load` raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblds.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EOVERFLOW, EBUSY = range(7)
+STATUS_NAMES = {0: "LDS_OK", 1: "LDS_EINVAL", 2: "LDS_ENOMEM", 3: "LDS_ECUDA", 4: "LDS_ETIMEOUT",
+                5: "LDS_EOVERFLOW", 6: "LDS_EBUSY"}
+DENSITY = {"edge": 0, "triangle": 1}
+PRECISION = {"exact": 0, "fp64": 1, "fp32": 2}
+MEM_HOST, MEM_DEVICE = 0, 1
+
+_lib = None
+
+
+class LdsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int64), ("input_pairs", ctypes.c_int64),
+                ("self_loops", ctypes.c_int64), ("duplicates", ctypes.c_int64), ("max_degree", ctypes.c_int32),
+                ("isolated", ctypes.c_int32), ("triangles", ctypes.c_int64)]
+
+
+class FwResult(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_void_p), ("R", ctypes.c_void_p), ("W", ctypes.c_void_p),
+                ("last", ctypes.c_void_p), ("D", ctypes.c_int64)]
+
+
+def _sig(lib, name, res, args):
+    fn = getattr(lib, name)
+    fn.restype = res
+    fn.argtypes = args
+    return fn
+
+
+def load():
+    """Loads liblds.so (once).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    _sig(lib, "lds_version", ctypes.c_char_p, [])
+    _sig(lib, "lds_last_error", ctypes.c_char_p, [])
+    _sig(lib, "lds_device_count", i32, [])
+    _sig(lib, "lds_create_graph", ctypes.c_int, [i32, i64, P, P, ctypes.c_int, P, ctypes.POINTER(P)])
+    _sig(lib, "lds_free", None, [P])
+    _sig(lib, "lds_graph_info", ctypes.c_int, [P, ctypes.POINTER(GraphInfo)])
+    _sig(lib, "lds_get_edges", ctypes.c_int, [P, P, P, ctypes.c_int])
+    _sig(lib, "lds_list_triangles", ctypes.c_int, [P, ctypes.POINTER(i64)])
+    _sig(lib, "lds_get_triangles", ctypes.c_int, [P, P, ctypes.c_int])
+    _sig(lib, "lds_core_numbers", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int])
+    _sig(lib, "lds_fw", ctypes.c_int, [P, ctypes.c_int, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(FwResult)])
+    _sig(lib, "lds_fw_last_timing", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)])
+    _sig(lib, "lds_set_pass_profiling", None, [i32])
+    _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
+    _sig(lib, "lds_launch_count", i64, [])
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise LdsError(status, load().lds_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())      # torch tensor
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def version() -> str:
+    return load().lds_version().decode()
+
+
+def device_count() -> int:
+    return int(load().lds_device_count())
+
+
+def set_pass_profiling(on: bool):
+    load().lds_set_pass_profiling(1 if on else 0)
+
+
+def launch_count() -> int:
+    return int(load().lds_launch_count())
+
+
+def debug_fail_alloc_after(k: int):
+    load().lds_debug_fail_alloc_after(int(k))
+
+
+class Graph:
+    """A graph handle (``lds_graph``).  ``src`` / ``dst`` are int32 numpy arrays
+    (host) or int32 torch CUDA tensors (device).  ``stream`` is a raw
+    cudaStream_t value (e.g. ``torch.cuda.current_stream().cuda_stream``)."""
+
+    def __init__(self, n: int, src, dst, stream: int | None = None):
+        lib = load()
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.int32)
+            dst = np.ascontiguousarray(dst, dtype=np.int32)
+            where = MEM_HOST
+        else:
+            where = MEM_DEVICE if _is_device(src) else MEM_HOST
+        m = len(src)
+        h = ctypes.c_void_p()
+        self._h = None
+        self.stream = stream
+        _check(lib.lds_create_graph(int(n), int(m), _ptr(src), _ptr(dst), where,
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self._h = h
+        info = self.info()
+        self.n = info["n"]
+        self.m = info["m"]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            load().lds_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def info(self) -> dict:
+        gi = GraphInfo()
+        _check(load().lds_graph_info(self._h, ctypes.byref(gi)))
+        return {f: getattr(gi, f) for f, _ in GraphInfo._fields_}
+
+    def edges(self):
+        u = np.empty(self.m, dtype=np.int32)
+        v = np.empty(self.m, dtype=np.int32)
+        _check(load().lds_get_edges(self._h, _ptr(u), _ptr(v), MEM_HOST))
+        return u, v
+
+    def list_triangles(self) -> int:
+        c = ctypes.c_int64()
+        _check(load().lds_list_triangles(self._h, ctypes.byref(c)))
+        return int(c.value)
+
+    def triangles(self):
+        t = self.list_triangles()
+        out = np.empty((t, 3), dtype=np.int32)
+        _check(load().lds_get_triangles(self._h, _ptr(out), MEM_HOST))
+        return out
+
+    def core_numbers(self, density: str = "edge"):
+        out = np.empty(self.n, dtype=np.int64)
+        _check(load().lds_core_numbers(self._h, DENSITY[density], _ptr(out), MEM_HOST))
+        return out
+
+    def fw(self, iters: int, density: str = "edge", precision: str = "exact",
+           want=("r", "R", "W", "last")):
+        """Frank-Wolfe (Alg. 1 / Alg. 6).  Returns a dict with the requested
+        arrays (host numpy) and the denominator D."""
+        n = self.n
+        npat = self.m if density == "edge" else (self.list_triangles() if "W" in want or "last" in want else 0)
+        res = FwResult()
+        out = {}
+        if "r" in want:
+            out["r"] = np.empty(n, dtype=np.float64)
+            res.r = out["r"].ctypes.data
+        if "R" in want:
+            out["R"] = np.empty(n, dtype=np.int64)
+            res.R = out["R"].ctypes.data
+        if "W" in want:
+            shape = (npat,) if density == "edge" else (npat, 3)
+            out["W"] = np.empty(shape, dtype=np.int64)
+            res.W = out["W"].ctypes.data
+        if "last" in want:
+            out["last"] = np.empty(npat, dtype=np.uint8)
+            res.last = out["last"].ctypes.data
+        _check(load().lds_fw(self._h, DENSITY[density], int(iters), PRECISION[precision], MEM_HOST,
+                             ctypes.byref(res)))
+        out["D"] = int(res.D)
+        return out
+
+    def fw_timing(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(load().lds_fw_last_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"fw_ms": a.value, "pass_us": b.value, "pass_launches": int(c.value)}
