@@ -137,10 +137,27 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
                   lds_fw_result* out);
 
 /* Times of the most recent lds_fw call on this handle, measured with CUDA events
- * on the handle's stream: total FW milliseconds and the average duration of the
- * dominant per-iteration kernel (the edge or triangle pass) in microseconds. */
+ * on the handle's stream (pass times only while lds_set_pass_profiling is on).
+ *   fw_ms          all iterations, from the first pass to the last fold
+ *   pass_us        average duration of the per-iteration pass kernel
+ *   pass_launches  number of pass launches timed
+ *   pass_bytes     algorithmic bytes one pass must move (the roofline numerator):
+ *                  every stored slot's column word, the per-chunk row index and
+ *                  bit-plane word, and one load (key) read per vertex
+ *   pass_kernel    name of the pass kernel used (static string)
+ * Any pointer may be NULL. */
 lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us,
-                              int64_t* pass_launches);
+                              int64_t* pass_launches, int64_t* pass_bytes, const char** pass_kernel);
+
+/* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
+ *   0  automatic: the degree-oriented pass (each edge once, stored at its
+ *      lower-degree endpoint, hot loads in shared memory) with 32-bit load
+ *      words when every scaled load fits 32 bits, else with 64-bit keys
+ *      (load, id), else variant 1;
+ *   1  the symmetric-CSR pass (each edge twice, once from each endpoint);
+ *   2  the degree-oriented pass with 64-bit keys.
+ * All compute the same iterates.  Errors: LDS_EINVAL. */
+lds_status lds_set_fw_variant(int32_t variant);
 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (process-wide counter; never fails). */

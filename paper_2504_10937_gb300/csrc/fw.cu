@@ -27,10 +27,12 @@
 #include <algorithm>
 #include <cmath>
 
-#include "graph.cuh"
+#include "fw_internal.cuh"
 #include "prims.cuh"
 
 namespace lds {
+
+int g_fw_variant = 0;
 
 namespace {
 
@@ -367,54 +369,11 @@ __global__ void widen_u32_kernel(const uint32_t* in, int64_t k, int64_t* out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = in[i];
 }
 
-struct PassTimer {
-    // Event pairs around every pass launch; read after the final sync.
-    std::vector<cudaEvent_t> ev;
-    int used = 0;
-    bool on = false;
-    void start(cudaStream_t s) {
-        if (!on) return;
-        if ((int)ev.size() < used + 2) {
-            cudaEvent_t a, b;
-            LDS_CUDA(cudaEventCreate(&a));
-            LDS_CUDA(cudaEventCreate(&b));
-            ev.push_back(a);
-            ev.push_back(b);
-        }
-        LDS_CUDA(cudaEventRecord(ev[used], s));
-    }
-    void stop(cudaStream_t s) {
-        if (!on) return;
-        LDS_CUDA(cudaEventRecord(ev[used + 1], s));
-        used += 2;
-    }
-    double total_ms() {
-        double t = 0;
-        for (int i = 0; i < used; i += 2) {
-            float ms = 0;
-            LDS_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-            t += ms;
-        }
-        return t;
-    }
-    ~PassTimer() {
-        for (auto e : ev) cudaEventDestroy(e);
-    }
-};
-
 int fw_grid(int64_t chunks) {
     int64_t want = (chunks + FW_UNROLL - 1) / FW_UNROLL;         // warps
     int64_t blocks = (want * 32 + FW_THREADS - 1) / FW_THREADS;
     int64_t cap = (int64_t)num_sms() * 8;                        // 8 resident blocks of 256 per SM
     return (int)std::max<int64_t>(1, std::min(blocks, cap));
-}
-
-int planes_capacity(int64_t plane_words, int N) {
-    // keep at most ~2 GiB of bit planes, at least 32 iterations
-    int64_t budget = (int64_t)2 << 30;
-    int64_t cap = plane_words > 0 ? budget / (plane_words * 4) : N;
-    cap = std::max<int64_t>(32, std::min<int64_t>(cap, 512));
-    return (int)std::min<int64_t>(cap, std::max(N, 1));
 }
 
 }  // namespace
@@ -624,15 +583,43 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
         out->D = Dn;
 
         if (d == LDS_EDGE) {
-            EdgeFwState st;
+            EdgeFwOut fo;
             LDS_CUDA(cudaEventRecord(e0, s));
+            bool fast = g_fw_variant != 1 &&
+                        run_edge_fw_oriented(g, iters, p, out->W != nullptr, out->last != nullptr, fo, timer);
+            if (fast) {
+                LDS_CUDA(cudaEventRecord(e1, s));
+                g->pass_bytes = 4 * g->m + 8 * ((g->m + 31) / 32) + 4 * g->fwv_nz +
+                                (std::string(g->pass_kernel) == "fw_opass32_kernel" ? 4 : 8) * (int64_t)nact;
+                if (out->r) {
+                    to_original_order_f64(g, fo.r_int.get(), r_orig.get());
+                    copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
+                }
+                if (out->R) {
+                    to_original_order_i64(g, fo.R_int.get(), R_orig.get());
+                    copy_out(out->R, where, R_orig.get(), n * sizeof(int64_t), s);
+                }
+                if (out->W && g->m) copy_out(out->W, where, fo.W_edge.get(), g->m * sizeof(int64_t), s);
+                if (out->last && g->m) copy_out(out->last, where, fo.last_edge.get(), g->m, s);
+                LDS_CUDA(cudaStreamSynchronize(s));
+            } else {
+            EdgeFwState st;
             run_edge_fw(g, iters, p, st, timer);
             LDS_CUDA(cudaEventRecord(e1, s));
+            {
+                const int64_t ns = 2 * g->m, nc = (ns + 31) / 32;
+                if (p == LDS_FP64) {
+                    g->pass_kernel = "fw64_slot_kernel";
+                    g->pass_bytes = 4 * ns + 4 * nc + 4 * nc + 16 * ns + 8 * (int64_t)nact;
+                } else {
+                    g->pass_kernel = "fw_edge_pass_kernel";
+                    g->pass_bytes = 4 * ns + 8 * nc + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
+                }
+            }
             const int64_t nslots = 2 * g->m;
             // exact loads of the returned weights
             if (nact) LDS_LAUNCH(loads_from_slots_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), st.W.get(), nact, R_int.get());
             if (n > nact) LDS_LAUNCH(pad_i64_kernel, grid_for(n - nact, blk), blk, 0, s, R_int.get(), nact, n);
-            LDS_CHECK_LAUNCH();
             if (out->r) {
                 if (p == LDS_EXACT)
                     LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
@@ -640,7 +627,6 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
                     LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
                 else
                     LDS_LAUNCH(loads_to_double_kernel<double>, grid_for(n, blk), blk, 0, s, st.r64.get(), nact, n, 1.0, r_int.get());
-                LDS_CHECK_LAUNCH();
                 to_original_order_f64(g, r_int.get(), r_orig.get());
                 copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
             }
@@ -653,9 +639,7 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
                 DevBuf<uint8_t> Ld(out->last ? g->m : 0, s);
                 const uint32_t* lastp = st.planes.get() + std::max<int64_t>(st.last_plane, 0) * ((nslots + 31) / 32);
                 LDS_LAUNCH(edge_weights_kernel, grid_for(g->m, blk), blk, 0, s, g->rowptr.get(), g->col.get(), g->eu.get(),
-                                                                        g->ev.get(), g->m, st.W.get(), lastp, Wd.get(),
-                                                                        Ld.get());
-                LDS_CHECK_LAUNCH();
+                           g->ev.get(), g->m, st.W.get(), lastp, Wd.get(), Ld.get());
                 if (out->W) copy_out(out->W, where, Wd.get(), g->m * sizeof(int64_t), s);
                 if (out->last) {
                     if (iters == 0) LDS_CUDA(cudaMemsetAsync(Ld.get(), 0, g->m, s));
@@ -663,12 +647,15 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
                 }
                 LDS_CUDA(cudaStreamSynchronize(s));
             }
+            }
         } else {
             ensure_triangles(g);
             TriFwState st;
             LDS_CUDA(cudaEventRecord(e0, s));
             run_tri_fw(g, iters, p, st, timer);
             LDS_CUDA(cudaEventRecord(e1, s));
+            g->pass_kernel = "fw_tri_pass_kernel";
+            g->pass_bytes = 12 * g->ntri + 8 * ((g->ntri + 31) / 32) + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
             const int64_t ntri = g->ntri;
             LDS_CUDA(cudaMemsetAsync(R_int.get(), 0, std::max(n, 1) * sizeof(int64_t), s));
             if (ntri) LDS_LAUNCH(tri_loads_from_w_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
@@ -714,15 +701,25 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
     });
 }
 
-lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us, int64_t* pass_launches) {
+lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us, int64_t* pass_launches,
+                              int64_t* pass_bytes, const char** pass_kernel) {
     return guard([&] {
         LDS_REQUIRE(g, LDS_EINVAL, "lds_fw_last_timing: NULL graph");
         if (fw_ms) *fw_ms = g->fw_ms;
         if (pass_us) *pass_us = g->pass_us;
         if (pass_launches) *pass_launches = g->pass_launches;
+        if (pass_bytes) *pass_bytes = g->pass_bytes;
+        if (pass_kernel) *pass_kernel = g->pass_kernel;
     });
 }
 
 void lds_set_pass_profiling(int32_t on) { g_pass_profiling = on != 0; }
+
+lds_status lds_set_fw_variant(int32_t variant) {
+    return guard([&] {
+        LDS_REQUIRE(variant >= 0 && variant <= 2, LDS_EINVAL, "lds_set_fw_variant: variant must be 0, 1 or 2");
+        g_fw_variant = variant;
+    });
+}
 
 }  // extern "C"

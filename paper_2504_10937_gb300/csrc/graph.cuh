@@ -29,15 +29,34 @@ struct lds_graph {
     int64_t ntri = -1;
     lds::DevBuf<int32_t> ta, tb, tc;
 
+    // FW view: vertices relabelled by (degree descending, id ascending); every
+    // edge stored once, in the row of its lower-ranked endpoint, pointing to the
+    // higher-ranked one (so most targets are high-degree vertices).
+    bool fwv_built = false;
+    int32_t fwv_bits = 0;              // B = bit length of nact (tie bits of a key)
+    int64_t fwv_nz = 0;                // non-empty rows
+    lds::DevBuf<int32_t> fwv_perm;     // [nact] fw id -> internal id
+    lds::DevBuf<int32_t> fwv_pos;      // [nact] internal id -> fw id
+    lds::DevBuf<int32_t> fwv_col;      // [m] target fw id; bit 31 on the first slot of each row
+    lds::DevBuf<int32_t> fwv_nzrow;    // [fwv_nz] fw id of each non-empty row, ascending
+    lds::DevBuf<int32_t> fwv_chunk_nz0;// [ceil(m / 32)] non-empty-row index of slot 32 g
+    lds::DevBuf<int64_t> fwv_edge;     // [m] canonical edge id of each slot
+    lds::DevBuf<int32_t> fwv_ta, fwv_tb, fwv_tc;  // triangles in fw ids (lazy)
+
     // timing of the most recent lds_fw
     double fw_ms = 0.0, pass_us = 0.0;
     int64_t pass_launches = 0;
+    int64_t pass_bytes = 0;
+    const char* pass_kernel = "";
 };
 
 namespace lds {
 
 // Builds slot_edge (canonical edge id of every CSR slot) if not present.
 void ensure_slot_edge(lds_graph* g);
+
+// Builds the FW view (see lds_graph) if not present.
+void ensure_fw_view(lds_graph* g);
 
 // Lists triangles into g->ta/tb/tc if not present.
 void ensure_triangles(lds_graph* g);

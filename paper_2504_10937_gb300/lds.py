@@ -73,10 +73,12 @@ def load():
     _sig(lib, "lds_core_numbers", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int])
     _sig(lib, "lds_fw", ctypes.c_int, [P, ctypes.c_int, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(FwResult)])
     _sig(lib, "lds_fw_last_timing", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double),
-                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)])
+                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                                   ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_char_p)])
     _sig(lib, "lds_set_pass_profiling", None, [i32])
     _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
     _sig(lib, "lds_launch_count", i64, [])
+    _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
     _lib = lib
     return lib
 
@@ -108,6 +110,11 @@ def device_count() -> int:
 
 def set_pass_profiling(on: bool):
     load().lds_set_pass_profiling(1 if on else 0)
+
+
+def set_fw_variant(variant: int):
+    """0: automatic (degree-oriented pass when the keys fit); 1: symmetric-CSR pass."""
+    _check(load().lds_set_fw_variant(int(variant)))
 
 
 def launch_count() -> int:
@@ -217,6 +224,9 @@ class Graph:
         return out
 
     def fw_timing(self):
-        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
-        _check(load().lds_fw_last_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return {"fw_ms": a.value, "pass_us": b.value, "pass_launches": int(c.value)}
+        a, b, c, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        k = ctypes.c_char_p()
+        _check(load().lds_fw_last_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(d), ctypes.byref(k)))
+        return {"fw_ms": a.value, "pass_us": b.value, "pass_launches": int(c.value),
+                "pass_bytes": int(d.value), "pass_kernel": (k.value or b"").decode()}

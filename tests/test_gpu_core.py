@@ -84,8 +84,15 @@ def test_degenerate_graphs(lds):
             assert g.triangles().shape == (0, 3)
 
 
+@pytest.fixture(params=[0, 1, 2], ids=["oriented32", "symmetric", "oriented64"])
+def variant(request, lds):
+    lds.set_fw_variant(request.param)
+    yield request.param
+    lds.set_fw_variant(0)
+
+
 @pytest.mark.parametrize("N", [0, 1, 2, 7, 33, 100])
-def test_fw_exact_bit_exact(lds, N):
+def test_fw_exact_bit_exact(lds, N, variant):
     for n, u, v in _graphs():
         with lds.Graph(n, u, v) as g:
             got = g.fw(N, precision="exact")
@@ -98,6 +105,20 @@ def test_fw_exact_bit_exact(lds, N):
                 assert np.array_equal(got["last"].astype(bool), ch[-1])
 
 
+def test_fw_beyond_the_shared_memory_hot_set(lds, variant):
+    # more than 16384 active vertices: gathers and counts also go through global memory
+    n, u, v, _ = synth.chung_lu(60000, 240000, 2.1, seed=6, n_blocks=4, block_size_range=(30, 90))
+    with lds.Graph(n, u, v) as g:
+        for N in (1, 25):
+            got = g.fw(N, precision="exact")
+            R, W, Dn, ch = ofw.fw_edge_exact(n, u, v, N, record=True)
+            assert np.array_equal(got["R"], R) and np.array_equal(got["W"], W)
+            assert np.array_equal(got["last"].astype(bool), ch[-1])
+            got32 = g.fw(N, precision="fp32")
+            r32, W32, _ = ofw.fw_edge_fp32(n, u, v, N)
+            assert np.array_equal(got32["r"], r32.astype(np.float64)) and np.array_equal(got32["W"], W32)
+
+
 def test_fw_exact_plane_folding_over_many_iterations(lds):
     # more iterations than the bit-plane buffer holds for small graphs (folds several times)
     n, u, v = _graphs()[1]
@@ -108,7 +129,7 @@ def test_fw_exact_plane_folding_over_many_iterations(lds):
 
 
 @pytest.mark.parametrize("N", [1, 5, 60])
-def test_fw_fp32_bit_exact(lds, N):
+def test_fw_fp32_bit_exact(lds, N, variant):
     for n, u, v in _graphs():
         with lds.Graph(n, u, v) as g:
             got = g.fw(N, precision="fp32")
