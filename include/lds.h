@@ -167,6 +167,34 @@ int64_t lds_launch_count(void);
  * that lds_fw_last_timing can report the pass kernel's average duration. */
 void lds_set_pass_profiling(int32_t on);
 
+/* Largest vertex count lds_fw_exact_noalloc accepts. */
+#define LDS_NOALLOC_MAX_VERTICES (1 << 20)
+
+/* The exact edge-density Frank-Wolfe iteration without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory themselves - a host framework that owns the whole
+ * device heap, a latency-critical loop that cannot take the implicit
+ * synchronisation of cudaMalloc / cudaFree, or a process whose memory budget is
+ * fixed at start-up.  It computes the same R and W as lds_fw(..., LDS_EDGE,
+ * iters, LDS_EXACT, ...), in one thread per edge.
+ *   n        vertices, 0 <= n <= LDS_NOALLOC_MAX_VERTICES (else LDS_EINVAL)
+ *   m, u, v  device int32[m] edges with 0 <= u[e] < v[e] < n, no repeats
+ *            (canonical edges as lds_get_edges returns them); else LDS_EINVAL
+ *   iters    0 <= iters <= 60000
+ *   R        device int64[n], output: scaled loads R_x = (iters+1)(iters+2) r_x
+ *   W        device int64[m], output: (iters+1)(iters+2) alpha_{u,v} per edge
+ *   stream   cudaStream_t for all work (NULL: default stream); the call returns
+ *            after the stream has finished it
+ * Scratch: a fixed device array of LDS_NOALLOC_MAX_VERTICES + 64 int32 words,
+ * held by every GPU that loads the library until the process exits; the call
+ * makes no cudaMalloc / cudaFree or other allocating call.  The first call on
+ * each device looks up the array's device address while that device is
+ * current; make that first call before any stream capture.  Every call on a
+ * device shares the array (each clears what it uses first), so calls that
+ * overlap on the GPU race: do not issue them concurrently. */
+lds_status lds_fw_exact_noalloc(int32_t n, int64_t m, const int32_t* u, const int32_t* v, int32_t iters,
+                                int64_t* R, int64_t* W, void* stream);
+
 /* Test hook: make the k-th device allocation from now fail with LDS_ENOMEM
  * (k <= 0 disables).  Host-side fault injection; no GPU fault involved. */
 void lds_debug_fail_alloc_after(int32_t k);
