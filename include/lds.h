@@ -149,6 +149,25 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
 lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us,
                               int64_t* pass_launches, int64_t* pass_bytes, const char** pass_kernel);
 
+/* Stable groups of the last lds_fw run on this handle (Alg. 2; Def. 5 for edge
+ * density, Def. 12 for triangle density) with the bounds of Lemma 4 / Lemma 8.
+ * Vertices are sorted by exact load descending, ties by id ascending; candidate
+ * groups end at the cut points (positions j whose prefix density beats every
+ * longer prefix); each candidate is checked on a modified feasible solution and
+ * merged with the next one when it fails.  Every output is a host array:
+ *   order      [n]  vertices in sorted order (original ids)
+ *   ngroups         number of accepted groups; group k covers positions
+ *                   [group_end[k-1], group_end[k]) (group_end[-1] = 0); positions
+ *                   after the last group form the unaccepted remainder
+ *   group_end  [n]  exclusive end positions
+ *   lo_num, hi_num [n]  lo_num[k] / D <= phi(u) <= hi_num[k] / D for u in group k
+ *   D               common denominator ((N+1)(N+2), or 3(N+1)(N+2) for triangles)
+ *   ncuts, cuts [n] number and 1-based positions of the cut points
+ * Any output pointer may be NULL.  Errors: LDS_EINVAL (no lds_fw run yet),
+ * LDS_EOVERFLOW (loads beyond the 64-bit sort key), LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_extract_sg(lds_graph* g, int32_t* order, int32_t* ngroups, int64_t* group_end, int64_t* lo_num,
+                          int64_t* hi_num, int64_t* D, int32_t* ncuts, int64_t* cuts);
+
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load

@@ -1,0 +1,614 @@
+// ExtractSG (Alg. 2): stable groups and compact-number bounds from the exact
+// feasible solution of the last Frank-Wolfe run on a handle.
+//
+// 1. Vertices are sorted by exact load R = D r descending, ties by id
+//    ascending (one radix sort of (Rmax - R, id) keys).
+// 2. e_j, the number of patterns (edges or triangles) inside the first j
+//    vertices, is a histogram over each pattern's largest position plus a scan.
+// 3. Position j is a cut point when e_j / j is strictly larger than e_j' / j'
+//    for every j' > j (argmax over j' >= j with ties to the larger j').  A tile
+//    reduction, a suffix pass over tiles and a per-tile suffix scan compare the
+//    fractions exactly with 128-bit cross products.
+// 4. Candidates (segments between cut points) are checked against Def. 5
+//    (Def. 12 for triangles) on a modified feasible solution: every pattern that
+//    touches the segment S and has a vertex after S (in Z) gives its weight to
+//    its lowest-load Z vertex; otherwise, if it has a vertex before S (in X),
+//    to its lowest-load S vertex; for an edge that is "all weight to the other
+//    endpoint".  S is accepted when every X vertex stays above max_S r' and
+//    every Z vertex below min_S r'; a failed candidate merges with the next one
+//    (Alg. 2's loop).  Each check is vertex-centric: the segment's vertices walk
+//    their edges (triangles), the S-side changes go to a per-position array and
+//    the outside changes become (segment, vertex) records that are sorted and
+//    summed.  The first round checks every candidate at once; a failure is
+//    followed by single checks of the growing merged segment.
+// 5. Accepted groups give lo = min_S R', hi = max_S R' (over the denominator D);
+//    by Lemma 4 / Lemma 8 lo <= D phi(u) <= hi for u in the group.
+#include <algorithm>
+#include <climits>
+
+#include "extract_sg.cuh"
+#include "prims.cuh"
+
+namespace lds {
+
+namespace {
+
+typedef __int128 i128;
+
+// a/b > c/d for b, d > 0 (the numerator -1 stands for minus infinity)
+__device__ __forceinline__ bool frac_gt(int64_t a, int64_t b, int64_t c, int64_t d) {
+    return (i128)a * (i128)d > (i128)c * (i128)b;
+}
+
+__global__ void rmax_kernel(const int64_t* R, int32_t n, unsigned long long* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long m = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        m = max(m, (unsigned long long)R[x]);
+    if (m) atomicMax(out, m);
+}
+
+// ties are broken by the original id (internal ids put isolated vertices last)
+__global__ void sg_keys_kernel(const int64_t* R, const int32_t* to_orig, int32_t n, uint64_t rmax, int bits,
+                               uint64_t* key) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        key[x] = ((rmax - (uint64_t)R[x]) << bits) | (uint64_t)to_orig[x];
+}
+
+__global__ void sg_order_kernel(const uint64_t* key, const int32_t* to_int, int32_t n, uint64_t mask, int32_t* order,
+                                int32_t* pos) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        int32_t x = to_int[(int32_t)(key[p] & mask)];
+        order[p] = x;
+        pos[x] = (int32_t)p;
+    }
+}
+
+__global__ void sg_hist_edges_kernel(const int32_t* eu, const int32_t* ev, int64_t m, const int32_t* pos, int32_t* h) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+        atomicAdd(h + max(pos[eu[e]], pos[ev[e]]), 1);
+}
+
+__global__ void sg_hist_tris_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t nt,
+                                    const int32_t* pos, int32_t* h) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += stride)
+        atomicAdd(h + max(pos[ta[t]], max(pos[tb[t]], pos[tc[t]])), 1);
+}
+
+constexpr int CUT_THREADS = 256;
+constexpr int CUT_ITEMS = 4;
+constexpr int CUT_TILE = CUT_THREADS * CUT_ITEMS;
+
+// excl_prefix[p] = patterns inside positions < p; e_{p+1} = excl_prefix[p] + h[p].
+__device__ __forceinline__ void frac_max(int64_t& a, int64_t& b, int64_t c, int64_t d) {
+    if (frac_gt(c, d, a, b)) { a = c; b = d; }
+}
+
+__global__ void cut_tilemax_kernel(const int64_t* incl, int32_t n, int64_t* tnum, int64_t* tden) {
+    __shared__ int64_t sn[CUT_THREADS], sd[CUT_THREADS];
+    int64_t base = (int64_t)blockIdx.x * CUT_TILE + threadIdx.x * CUT_ITEMS;
+    int64_t bn = -1, bd = 1;
+    for (int k = 0; k < CUT_ITEMS; ++k) {
+        int64_t p = base + k;
+        if (p < n) frac_max(bn, bd, incl[p], p + 1);
+    }
+    sn[threadIdx.x] = bn;
+    sd[threadIdx.x] = bd;
+    __syncthreads();
+    for (int o = CUT_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            int64_t a = sn[threadIdx.x], b = sd[threadIdx.x];
+            frac_max(a, b, sn[threadIdx.x + o], sd[threadIdx.x + o]);
+            sn[threadIdx.x] = a;
+            sd[threadIdx.x] = b;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tnum[blockIdx.x] = sn[0];
+        tden[blockIdx.x] = sd[0];
+    }
+}
+
+// suffix max over tiles, exclusive: sfx[b] = max over tiles > b (one thread; tiles are few)
+__global__ void cut_tile_suffix_kernel(const int64_t* tnum, const int64_t* tden, int64_t ntiles, int64_t* snum,
+                                       int64_t* sden) {
+    if (blockIdx.x || threadIdx.x) return;
+    int64_t a = -1, b = 1;
+    for (int64_t t = ntiles - 1; t >= 0; --t) {
+        snum[t] = a;
+        sden[t] = b;
+        frac_max(a, b, tnum[t], tden[t]);
+    }
+}
+
+__global__ void cut_flags_kernel(const int64_t* incl, int32_t n, const int64_t* snum, const int64_t* sden,
+                                 int32_t* flag) {
+    __shared__ int64_t sn[CUT_THREADS], sd[CUT_THREADS];
+    const int t = threadIdx.x;
+    int64_t base = (int64_t)blockIdx.x * CUT_TILE + t * CUT_ITEMS;
+    // max of this thread's items
+    int64_t mn = -1, md = 1;
+    for (int k = 0; k < CUT_ITEMS; ++k) {
+        int64_t p = base + k;
+        if (p < n) frac_max(mn, md, incl[p], p + 1);
+    }
+    sn[t] = mn;
+    sd[t] = md;
+    __syncthreads();
+    // exclusive suffix max over threads t+1.. (Hillis-Steele on a reversed scan)
+    int64_t an = mn, ad = md;       // inclusive suffix value
+    for (int o = 1; o < CUT_THREADS; o <<= 1) {
+        int64_t cn = -1, cd = 1;
+        if (t + o < CUT_THREADS) { cn = sn[t + o]; cd = sd[t + o]; }
+        __syncthreads();
+        frac_max(an, ad, cn, cd);
+        sn[t] = an;
+        sd[t] = ad;
+        __syncthreads();
+    }
+    int64_t rn = snum[blockIdx.x], rd = sden[blockIdx.x];
+    if (t + 1 < CUT_THREADS) frac_max(rn, rd, sn[t + 1], sd[t + 1]);
+    for (int k = CUT_ITEMS - 1; k >= 0; --k) {
+        int64_t p = base + k;
+        if (p >= n) continue;
+        int64_t en = incl[p], ed = p + 1;
+        flag[p] = frac_gt(en, ed, rn, rd) ? 1 : 0;
+        frac_max(rn, rd, en, ed);
+    }
+}
+
+__global__ void cut_list_kernel(const int32_t* flag, const int64_t* excl, int32_t n, int64_t* cuts) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        if (flag[p]) cuts[excl[p]] = p + 1;
+}
+
+// ---- checks
+
+__global__ void seg_of_pos_kernel(const int64_t* sa, const int64_t* sb, int32_t nseg, int32_t n, int32_t* segof) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        int lo = 0, hi = nseg;            // last segment with sa <= p
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (sa[mid] <= p) lo = mid + 1; else hi = mid;
+        }
+        int s = lo - 1;
+        segof[p] = (s >= 0 && p <= sb[s]) ? s : -1;
+    }
+}
+
+struct Rec {
+    uint64_t* key;
+    int64_t* val;
+    unsigned long long* count;
+    int64_t cap;
+};
+
+__device__ __forceinline__ void push_rec(const Rec& r, uint64_t key, int64_t val) {
+    unsigned long long i = atomicAdd(r.count, 1ull);
+    if ((int64_t)i < r.cap) {
+        r.key[i] = key;
+        r.val[i] = val;
+    }
+}
+
+// edge check, one thread per position of a checked segment
+__global__ void check_edges_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof, const int64_t* sa,
+                                   const int64_t* sb, int32_t npos_lo, int32_t npos_hi, const int64_t* rowptr,
+                                   const int32_t* col, const int64_t* slot_edge, const int32_t* eu, const int64_t* W,
+                                   int64_t Dn, int32_t n, int32_t nact, int64_t* deltaS, Rec rec, bool count_only) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
+        int32_t s = segof[p];
+        if (s < 0) continue;
+        int32_t x = order[p];
+        if (x < nact) {                              // isolated vertices have no row
+            int64_t a = sa[s], b = sb[s];
+            int64_t d = 0;
+            for (int64_t q = rowptr[x], e = rowptr[x + 1]; q < e; ++q) {
+                int32_t y = col[q];
+                int64_t py = pos[y];
+                if (py >= a && py <= b) continue;
+                int64_t ed = slot_edge[q];
+                int64_t share_x = (eu[ed] == x) ? W[ed] : Dn - W[ed];
+                int64_t share_y = Dn - share_x;
+                if (count_only) {
+                    atomicAdd(rec.count, 1ull);
+                } else if (py < a) {                 // y in X: the edge goes to x
+                    d += share_y;
+                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)y, -share_y);
+                } else {                             // y in Z: the edge goes to y
+                    d -= share_x;
+                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)y, share_x);
+                }
+            }
+            if (!count_only) deltaS[p] = d;
+        }
+    }
+}
+
+// triangle check: a triangle touching segment s is handled by its member of s
+// with the largest position
+__global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof, const int64_t* sa,
+                                  const int64_t* sb, int32_t npos_lo, int32_t npos_hi, const int64_t* vt_ptr,
+                                  const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                  const int64_t* W, int32_t n, int32_t nact, unsigned long long* deltaS, Rec rec,
+                                  bool count_only) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
+        int32_t s = segof[p];
+        if (s < 0) continue;
+        int32_t x = order[p];
+        if (x >= nact) continue;                     // isolated vertices lie in no triangle
+        int64_t a = sa[s], b = sb[s];
+        for (int64_t q = vt_ptr[x], e = vt_ptr[x + 1]; q < e; ++q) {
+            int32_t t = vt_idx[q];
+            int32_t v[3] = {ta[t], tb[t], tc[t]};
+            int64_t pp[3] = {pos[v[0]], pos[v[1]], pos[v[2]]};
+            // owner: the member of s with the largest position
+            int64_t best = -1;
+            for (int k = 0; k < 3; ++k)
+                if (pp[k] >= a && pp[k] <= b && pp[k] > best) best = pp[k];
+            if (best != p) continue;
+            int zt = -1, st = -1;
+            bool anyx = false;
+            for (int k = 0; k < 3; ++k) {
+                if (pp[k] > b) { if (zt < 0 || pp[k] > pp[zt]) zt = k; }
+                else if (pp[k] < a) anyx = true;
+                else if (st < 0 || pp[k] > pp[st]) st = k;
+            }
+            int tgt;
+            if (zt >= 0) tgt = zt;
+            else if (anyx) tgt = st;
+            else continue;
+            int64_t moved = 0;
+            for (int k = 0; k < 3; ++k) {
+                bool mover = (zt >= 0) ? !(pp[k] > b) : (pp[k] < a);
+                if (!mover) continue;
+                int64_t w = W[3 * (int64_t)t + k];
+                moved += w;
+                if (pp[k] >= a && pp[k] <= b) {
+                    if (!count_only) atomicAdd(deltaS + pp[k], (unsigned long long)(-w));
+                } else if (count_only) {
+                    atomicAdd(rec.count, 1ull);
+                } else {
+                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)v[k], -w);
+                }
+            }
+            if (pp[tgt] >= a && pp[tgt] <= b) {
+                if (!count_only) atomicAdd(deltaS + pp[tgt], (unsigned long long)moved);
+            } else if (count_only) {
+                atomicAdd(rec.count, 1ull);
+            } else {
+                push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)v[tgt], moved);
+            }
+        }
+    }
+}
+
+__global__ void iota_u32_kernel(uint32_t* p, int64_t k) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) p[i] = (uint32_t)i;
+}
+
+__global__ void rec_gather_vals_kernel(const int64_t* val, const uint32_t* idx, int64_t k, int64_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = val[idx[i]];
+}
+
+__global__ void rec_reduce_kernel(const uint64_t* key, const int64_t* val, int64_t k, int32_t n, const int64_t* R,
+                                  const int32_t* pos, const int64_t* sa, long long* minX, long long* maxZ) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        uint64_t kk = key[i];
+        if (i > 0 && key[i - 1] == kk) continue;
+        int64_t tot = 0;
+        for (int64_t j = i; j < k && key[j] == kk; ++j) tot += val[j];
+        int32_t s = (int32_t)(kk / (uint64_t)n);
+        int32_t y = (int32_t)(kk % (uint64_t)n);
+        long long v = (long long)(R[y] + tot);
+        if (pos[y] < sa[s]) atomicMin(minX + s, v);
+        else atomicMax(maxZ + s, v);
+    }
+}
+
+__global__ void side_s_kernel(const int32_t* order, const int32_t* segof, int32_t npos_lo, int32_t npos_hi,
+                              const int64_t* R, const int64_t* deltaS, long long* minS, long long* maxS) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
+        int32_t s = segof[p];
+        if (s < 0) continue;
+        long long v = (long long)(R[order[p]] + deltaS[p]);
+        atomicMin(minS + s, v);
+        atomicMax(maxS + s, v);
+    }
+}
+
+__global__ void side_init_kernel(const int64_t* sa, const int64_t* sb, int32_t nseg, int32_t n, const int32_t* order,
+                                 const int64_t* R, long long* minS, long long* maxS, long long* minX, long long* maxZ) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nseg; s += stride) {
+        minS[s] = LLONG_MAX;
+        maxS[s] = LLONG_MIN;
+        minX[s] = sa[s] > 0 ? (long long)R[order[sa[s] - 1]] : LLONG_MAX;
+        maxZ[s] = sb[s] < n - 1 ? (long long)R[order[sb[s] + 1]] : LLONG_MIN;
+    }
+}
+
+__global__ void vt_key_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t nt, uint64_t* key,
+                              uint32_t* tid) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nt; i += stride) {
+        int64_t t = i / 3;
+        int k = (int)(i % 3);
+        key[i] = (uint64_t)(k == 0 ? ta[t] : (k == 1 ? tb[t] : tc[t]));
+        tid[i] = (uint32_t)t;
+    }
+}
+
+__global__ void vt_ptr_kernel(const uint64_t* key, int64_t k3, int32_t nact, int64_t* ptr) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k3; i += stride) {
+        int64_t x = (int64_t)key[i];
+        int64_t prev = i == 0 ? -1 : (int64_t)key[i - 1];
+        for (int64_t r = prev + 1; r <= x; ++r) ptr[r] = i;
+        if (i == k3 - 1)
+            for (int64_t r = x + 1; r <= nact; ++r) ptr[r] = k3;
+    }
+}
+
+__global__ void u32_to_i32_kernel(const uint32_t* in, int64_t k, int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (int32_t)in[i];
+}
+
+}  // namespace
+
+void ensure_vertex_triangles(lds_graph* g) {
+    if (g->vt_ptr.p) return;
+    ensure_triangles(g);
+    cudaStream_t s = g->stream;
+    const int32_t nact = g->nact;
+    const int64_t nt = g->ntri;
+    const int blk = 256;
+    g->vt_ptr.alloc(nact + 1, s);
+    g->vt_idx.alloc(std::max<int64_t>(3 * nt, 1), s);
+    if (nt == 0) {
+        LDS_CUDA(cudaMemsetAsync(g->vt_ptr.get(), 0, (nact + 1) * sizeof(int64_t), s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
+    DevBuf<uint64_t> key(3 * nt, s);
+    DevBuf<uint32_t> tid(3 * nt, s);
+    LDS_LAUNCH(vt_key_kernel, grid_for(3 * nt, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), nt, key.get(),
+               tid.get());
+    radix_sort_u64(key.get(), tid.get(), 3 * nt, bit_length_u64((uint64_t)nact), s);
+    LDS_LAUNCH(vt_ptr_kernel, grid_for(3 * nt, blk), blk, 0, s, key.get(), 3 * nt, nact, g->vt_ptr.get());
+    LDS_LAUNCH(u32_to_i32_kernel, grid_for(3 * nt, blk), blk, 0, s, tid.get(), 3 * nt, g->vt_idx.get());
+    LDS_CUDA(cudaStreamSynchronize(s));
+}
+
+// Checks the given disjoint segments (positions, inclusive) and returns
+// (minS, maxS, minX, maxZ) per segment.
+static void check_segments(lds_graph* g, const SgState& st, const std::vector<int64_t>& ha,
+                           const std::vector<int64_t>& hb, std::vector<long long>& minS, std::vector<long long>& maxS,
+                           std::vector<long long>& minX, std::vector<long long>& maxZ) {
+    cudaStream_t s = g->stream;
+    const int blk = 256;
+    const int32_t n = g->n;
+    const int32_t nseg = (int32_t)ha.size();
+    const bool tri = g->fw_density == LDS_TRIANGLE;
+    DevBuf<int64_t> sa(nseg, s), sb(nseg, s);
+    copy_in(sa.get(), ha.data(), LDS_MEM_HOST, nseg * sizeof(int64_t), s);
+    copy_in(sb.get(), hb.data(), LDS_MEM_HOST, nseg * sizeof(int64_t), s);
+    const int32_t plo = (int32_t)ha.front(), phi = (int32_t)hb.back() + 1;
+    DevBuf<int32_t> segof(n, s);
+    LDS_LAUNCH(seg_of_pos_kernel, grid_for(n, blk), blk, 0, s, sa.get(), sb.get(), nseg, n, segof.get());
+    DevBuf<int64_t> deltaS(n, s);
+    LDS_CUDA(cudaMemsetAsync(deltaS.get(), 0, n * sizeof(int64_t), s));
+    DevBuf<unsigned long long> rcnt(1, s);
+    const int64_t* W = g->fw_W.get();
+    const int32_t nact = g->nact;
+    // two passes: count the records, then fill an exactly sized buffer
+    DevBuf<uint64_t> rkey;
+    DevBuf<int64_t> rval;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool count_only = pass == 0;
+        int64_t cap = 0;
+        if (!count_only) {
+            unsigned long long c = 0;
+            LDS_CUDA(cudaMemcpyAsync(&c, rcnt.get(), sizeof(c), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            cap = (int64_t)c;
+            rkey.alloc(std::max<int64_t>(cap, 1), s);
+            rval.alloc(std::max<int64_t>(cap, 1), s);
+        }
+        LDS_CUDA(cudaMemsetAsync(rcnt.get(), 0, sizeof(unsigned long long), s));
+        Rec rec{rkey.get(), rval.get(), rcnt.get(), cap};
+        if (!tri) {
+            if (g->m) {
+                ensure_slot_edge(g);
+                LDS_LAUNCH(check_edges_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(),
+                           segof.get(), sa.get(), sb.get(), plo, phi, g->rowptr.get(), g->col.get(), g->slot_edge.get(),
+                           g->eu.get(), W, g->fw_D, n, nact, deltaS.get(), rec, count_only);
+            }
+        } else if (g->ntri) {
+            ensure_vertex_triangles(g);
+            LDS_LAUNCH(check_tris_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(), segof.get(),
+                       sa.get(), sb.get(), plo, phi, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(), g->tb.get(),
+                       g->tc.get(), W, n, nact, (unsigned long long*)deltaS.get(), rec, count_only);
+        }
+    }
+    const int64_t cap = (int64_t)rkey.n;
+    unsigned long long nrec = 0;
+    LDS_CUDA(cudaMemcpyAsync(&nrec, rcnt.get(), sizeof(nrec), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    LDS_REQUIRE((int64_t)nrec <= cap, LDS_ECUDA, "extract_sg: record buffer overflow (internal error)");
+    DevBuf<long long> dminS(nseg, s), dmaxS(nseg, s), dminX(nseg, s), dmaxZ(nseg, s);
+    LDS_LAUNCH(side_init_kernel, grid_for(nseg, blk), blk, 0, s, sa.get(), sb.get(), nseg, n, st.order.get(),
+               g->fw_R.get(), dminS.get(), dmaxS.get(), dminX.get(), dmaxZ.get());
+    if (nrec) {
+        DevBuf<uint32_t> idx(nrec, s);
+        DevBuf<int64_t> sval(nrec, s);
+        // sort the records by (segment, vertex), carrying their index
+        LDS_LAUNCH(iota_u32_kernel, grid_for((int64_t)nrec, blk), blk, 0, s, idx.get(), (int64_t)nrec);
+        radix_sort_u64(rkey.get(), idx.get(), (int64_t)nrec, bit_length_u64((uint64_t)nseg * (uint64_t)n), s);
+        LDS_LAUNCH(rec_gather_vals_kernel, grid_for((int64_t)nrec, blk), blk, 0, s, rval.get(), idx.get(), (int64_t)nrec,
+                   sval.get());
+        LDS_LAUNCH(rec_reduce_kernel, grid_for((int64_t)nrec, blk), blk, 0, s, rkey.get(), sval.get(), (int64_t)nrec, n,
+                   g->fw_R.get(), st.pos.get(), sa.get(), dminX.get(), dmaxZ.get());
+    }
+    LDS_LAUNCH(side_s_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), segof.get(), plo, phi, g->fw_R.get(),
+               deltaS.get(), dminS.get(), dmaxS.get());
+    minS.resize(nseg);
+    maxS.resize(nseg);
+    minX.resize(nseg);
+    maxZ.resize(nseg);
+    LDS_CUDA(cudaMemcpyAsync(minS.data(), dminS.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaMemcpyAsync(maxS.data(), dmaxS.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaMemcpyAsync(minX.data(), dminX.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaMemcpyAsync(maxZ.data(), dmaxZ.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+}
+
+void extract_sg(lds_graph* g, SgState& st) {
+    LDS_REQUIRE(g->fw_valid, LDS_EINVAL, "extract_sg: run lds_fw on this graph first");
+    cudaStream_t s = g->stream;
+    const int blk = 256;
+    const int32_t n = g->n;
+    const bool tri = g->fw_density == LDS_TRIANGLE;
+    st.D = g->fw_D;
+    st.order.alloc(std::max(n, 1), s);
+    st.pos.alloc(std::max(n, 1), s);
+    st.cuts.clear();
+    st.group_end.clear();
+    st.lo.clear();
+    st.hi.clear();
+    if (n == 0) return;
+    // 1. order by (R desc, id asc)
+    DevBuf<unsigned long long> rmax(1, s);
+    LDS_CUDA(cudaMemsetAsync(rmax.get(), 0, sizeof(unsigned long long), s));
+    LDS_LAUNCH(rmax_kernel, grid_for(n, blk), blk, 0, s, g->fw_R.get(), n, rmax.get());
+    unsigned long long hrmax = 0;
+    LDS_CUDA(cudaMemcpyAsync(&hrmax, rmax.get(), sizeof(hrmax), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    const int idbits = std::max(1, bit_length_u64((uint64_t)std::max(n - 1, 1)));
+    const int rbits = bit_length_u64(hrmax);
+    LDS_REQUIRE(rbits + idbits <= 64, LDS_EOVERFLOW, "extract_sg: loads too large for the sort key");
+    {
+        DevBuf<uint64_t> key(n, s);
+        LDS_LAUNCH(sg_keys_kernel, grid_for(n, blk), blk, 0, s, g->fw_R.get(), g->to_orig.get(), n, (uint64_t)hrmax,
+                   idbits, key.get());
+        radix_sort_u64(key.get(), nullptr, n, rbits + idbits, s);
+        LDS_LAUNCH(sg_order_kernel, grid_for(n, blk), blk, 0, s, key.get(), g->to_int.get(), n, (1ull << idbits) - 1ull,
+                   st.order.get(), st.pos.get());
+    }
+    // 2. e_j
+    DevBuf<int32_t> h(n, s);
+    LDS_CUDA(cudaMemsetAsync(h.get(), 0, n * sizeof(int32_t), s));
+    if (!tri && g->m)
+        LDS_LAUNCH(sg_hist_edges_kernel, grid_for(g->m, blk), blk, 0, s, g->eu.get(), g->ev.get(), g->m, st.pos.get(), h.get());
+    if (tri && g->ntri)
+        LDS_LAUNCH(sg_hist_tris_kernel, grid_for(g->ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), g->ntri,
+                   st.pos.get(), h.get());
+    DevBuf<int64_t> incl(n + 1, s);
+    {
+        DevBuf<int32_t> h1(n + 1, s);
+        LDS_CUDA(cudaMemsetAsync(h1.get(), 0, (n + 1) * sizeof(int32_t), s));
+        LDS_CUDA(cudaMemcpyAsync(h1.get(), h.get(), n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        // exclusive scan of [h0, h1, ..., 0]: entry p + 1 is the inclusive prefix up to p
+        exclusive_scan_i32_to_i64(h1.get(), incl.get(), n + 1, s);
+    }
+    const int64_t* inclp = incl.get() + 1;     // inclp[p] = e_{p+1}
+    // 3. cut points
+    const int64_t ntiles = (n + CUT_TILE - 1) / CUT_TILE;
+    DevBuf<int64_t> tn(ntiles, s), td(ntiles, s), sn(ntiles, s), sd(ntiles, s);
+    LDS_LAUNCH(cut_tilemax_kernel, (unsigned)ntiles, CUT_THREADS, 0, s, inclp, n, tn.get(), td.get());
+    LDS_LAUNCH(cut_tile_suffix_kernel, 1, 1, 0, s, tn.get(), td.get(), ntiles, sn.get(), sd.get());
+    DevBuf<int32_t> flag(n, s);
+    LDS_LAUNCH(cut_flags_kernel, (unsigned)ntiles, CUT_THREADS, 0, s, inclp, n, sn.get(), sd.get(), flag.get());
+    DevBuf<int64_t> fex(n, s);
+    int64_t ncut = exclusive_scan_i32_to_i64(flag.get(), fex.get(), n, s);
+    DevBuf<int64_t> dcuts(std::max<int64_t>(ncut, 1), s);
+    LDS_LAUNCH(cut_list_kernel, grid_for(n, blk), blk, 0, s, flag.get(), fex.get(), n, dcuts.get());
+    st.cuts.resize(ncut);
+    LDS_CUDA(cudaMemcpyAsync(st.cuts.data(), dcuts.get(), ncut * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    // 4. checks: every candidate alone first, then the merged segments of failures
+    std::vector<int64_t> ca, cb;
+    int64_t prev = 0;
+    for (int64_t c : st.cuts) {
+        ca.push_back(prev);
+        cb.push_back(c - 1);
+        prev = c;
+    }
+    std::vector<long long> mnS, mxS, mnX, mxZ;
+    check_segments(g, st, ca, cb, mnS, mxS, mnX, mxZ);
+    auto passes = [&](size_t i, int64_t a, int64_t b) {
+        bool ok = true;
+        if (a > 0) ok &= mnX[i] > mxS[i];
+        if (b < n - 1) ok &= mxZ[i] < mnS[i];
+        return ok;
+    };
+    int64_t start = 0;
+    for (size_t k = 0; k < ca.size(); ++k) {
+        long long lo, hi;
+        bool ok;
+        if (ca[k] == start) {
+            ok = passes(k, ca[k], cb[k]);
+            lo = mnS[k];
+            hi = mxS[k];
+        } else {
+            std::vector<int64_t> a1{start}, b1{cb[k]};
+            std::vector<long long> s1, s2, s3, s4;
+            check_segments(g, st, a1, b1, s1, s2, s3, s4);
+            ok = true;
+            if (start > 0) ok &= s3[0] > s2[0];
+            if (cb[k] < n - 1) ok &= s4[0] < s1[0];
+            lo = s1[0];
+            hi = s2[0];
+        }
+        if (ok) {
+            st.group_end.push_back(cb[k] + 1);
+            st.lo.push_back(lo);
+            st.hi.push_back(hi);
+            start = cb[k] + 1;
+        }
+    }
+}
+
+}  // namespace lds
+
+using namespace lds;
+
+extern "C" lds_status lds_extract_sg(lds_graph* g, int32_t* order, int32_t* ngroups, int64_t* group_end,
+                                     int64_t* lo_num, int64_t* hi_num, int64_t* D, int32_t* ncuts, int64_t* cuts) {
+    return guard([&] {
+        LDS_REQUIRE(g && ngroups, LDS_EINVAL, "lds_extract_sg: NULL argument");
+        SgState st;
+        extract_sg(g, st);
+        const int32_t n = g->n;
+        *ngroups = (int32_t)st.group_end.size();
+        if (D) *D = st.D;
+        if (ncuts) *ncuts = (int32_t)st.cuts.size();
+        if (order && n) {
+            DevBuf<int32_t> o(n, g->stream);
+            map_ids(st.order.get(), g->to_orig.get(), n, o.get(), g->stream);
+            copy_out(order, LDS_MEM_HOST, o.get(), n * sizeof(int32_t), g->stream);
+            LDS_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        for (size_t k = 0; k < st.group_end.size(); ++k) {
+            if (group_end) group_end[k] = st.group_end[k];
+            if (lo_num) lo_num[k] = st.lo[k];
+            if (hi_num) hi_num[k] = st.hi[k];
+        }
+        if (cuts)
+            for (size_t k = 0; k < st.cuts.size(); ++k) cuts[k] = st.cuts[k];
+    });
+}

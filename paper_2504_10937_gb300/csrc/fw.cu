@@ -553,6 +553,111 @@ static void run_tri_fw(lds_graph* g, int N, lds_precision p, TriFwState& st, Pas
     }
 }
 
+void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool want_last) {
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n, nact = g->nact;
+    const int blk = 256;
+    PassTimer timer;
+    timer.on = g_pass_profiling;
+    cudaEvent_t e0, e1;
+    LDS_CUDA(cudaEventCreate(&e0));
+    LDS_CUDA(cudaEventCreate(&e1));
+    struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{e0, e1};
+
+    g->fw_valid = false;
+    const int64_t Dn = (int64_t)(iters + 1) * (iters + 2) * (d == LDS_TRIANGLE ? 3 : 1);
+    g->fw_R.alloc(std::max(n, 1), s);
+    g->fw_r.alloc(std::max(n, 1), s);
+    g->fw_last.release();
+    DevBuf<int64_t>& R_int = g->fw_R;
+    DevBuf<double>& r_int = g->fw_r;
+
+    if (d == LDS_EDGE) {
+        EdgeFwOut fo;
+        LDS_CUDA(cudaEventRecord(e0, s));
+        bool fast = g_fw_variant != 1 && run_edge_fw_oriented(g, iters, p, true, want_last, fo, timer);
+        if (fast) {
+            LDS_CUDA(cudaEventRecord(e1, s));
+            g->pass_bytes = 4 * g->m + 8 * ((g->m + 31) / 32) + 4 * g->fwv_nz +
+                            (std::string(g->pass_kernel) == "fw_opass32_kernel" ? 4 : 8) * (int64_t)nact;
+            R_int = std::move(fo.R_int);
+            r_int = std::move(fo.r_int);
+            g->fw_W = std::move(fo.W_edge);
+            if (want_last) g->fw_last = std::move(fo.last_edge);
+        } else {
+            EdgeFwState st;
+            run_edge_fw(g, iters, p, st, timer);
+            LDS_CUDA(cudaEventRecord(e1, s));
+            const int64_t nslots = 2 * g->m, nc = (nslots + 31) / 32;
+            if (p == LDS_FP64) {
+                g->pass_kernel = "fw64_slot_kernel";
+                g->pass_bytes = 4 * nslots + 8 * nc + 16 * nslots + 8 * (int64_t)nact;
+            } else {
+                g->pass_kernel = "fw_edge_pass_kernel";
+                g->pass_bytes = 4 * nslots + 8 * nc + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
+            }
+            if (nact) LDS_LAUNCH(loads_from_slots_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), st.W.get(), nact, R_int.get());
+            if (n > nact) LDS_LAUNCH(pad_i64_kernel, grid_for(n - nact, blk), blk, 0, s, R_int.get(), nact, n);
+            if (n) {
+                if (p == LDS_EXACT)
+                    LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
+                else if (p == LDS_FP32)
+                    LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
+                else
+                    LDS_LAUNCH(loads_to_double_kernel<double>, grid_for(n, blk), blk, 0, s, st.r64.get(), nact, n, 1.0, r_int.get());
+            }
+            g->fw_W.alloc(std::max<int64_t>(g->m, 1), s);
+            if (want_last) g->fw_last.alloc(std::max<int64_t>(g->m, 1), s);
+            if (g->m) {
+                const uint32_t* lastp = st.planes.get() + std::max<int64_t>(st.last_plane, 0) * nc;
+                LDS_LAUNCH(edge_weights_kernel, grid_for(g->m, blk), blk, 0, s, g->rowptr.get(), g->col.get(), g->eu.get(),
+                           g->ev.get(), g->m, st.W.get(), lastp, g->fw_W.get(), want_last ? g->fw_last.get() : nullptr);
+                if (want_last && iters == 0) LDS_CUDA(cudaMemsetAsync(g->fw_last.get(), 0, g->m, s));
+            }
+        }
+    } else {
+        ensure_triangles(g);
+        TriFwState st;
+        LDS_CUDA(cudaEventRecord(e0, s));
+        run_tri_fw(g, iters, p, st, timer);
+        LDS_CUDA(cudaEventRecord(e1, s));
+        g->pass_kernel = "fw_tri_pass_kernel";
+        g->pass_bytes = 12 * g->ntri + 8 * ((g->ntri + 31) / 32) + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
+        const int64_t ntri = g->ntri;
+        LDS_CUDA(cudaMemsetAsync(R_int.get(), 0, std::max(n, 1) * sizeof(int64_t), s));
+        if (ntri)
+            LDS_LAUNCH(tri_loads_from_w_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
+                       st.W.get(), (unsigned long long*)R_int.get());
+        if (n) {
+            if (p == LDS_EXACT)
+                LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
+            else
+                LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
+        }
+        g->fw_W.alloc(std::max<int64_t>(3 * ntri, 1), s);
+        if (ntri) LDS_LAUNCH(widen_u32_kernel, grid_for(3 * ntri, blk), blk, 0, s, st.W.get(), 3 * ntri, g->fw_W.get());
+        if (want_last) {
+            g->fw_last.alloc(std::max<int64_t>(ntri, 1), s);
+            int64_t nch = (ntri + 31) / 32;
+            const uint32_t* p0 = st.planes.get() + 2 * std::max<int64_t>(st.last_pair, 0) * nch;
+            if (ntri) {
+                if (iters == 0) LDS_CUDA(cudaMemsetAsync(g->fw_last.get(), 2, ntri, s));
+                else LDS_LAUNCH(tri_last_kernel, grid_for(ntri, blk), blk, 0, s, p0, p0 + nch, ntri, g->fw_last.get());
+            }
+        }
+    }
+    LDS_CUDA(cudaStreamSynchronize(s));
+    float ms = 0;
+    LDS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    g->fw_ms = ms;
+    g->pass_launches = timer.used / 2;
+    g->pass_us = timer.used ? 1000.0 * timer.total_ms() / (timer.used / 2) : 0.0;
+    g->fw_valid = true;
+    g->fw_density = d;
+    g->fw_iters = iters;
+    g->fw_D = Dn;
+}
+
 }  // namespace lds
 
 using namespace lds;
@@ -567,137 +672,26 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
         LDS_REQUIRE(iters >= 0 && iters <= (d == LDS_EDGE ? 60000 : 30000), LDS_EINVAL,
                     "lds_fw: iters = %d out of range", iters);
         LDS_REQUIRE(where == LDS_MEM_HOST || where == LDS_MEM_DEVICE, LDS_EINVAL, "lds_fw: bad lds_mem");
+        fw_run(g, d, iters, p, out->last != nullptr);
         cudaStream_t s = g->stream;
-        const int32_t n = g->n, nact = g->nact;
-        const int blk = 256;
-        PassTimer timer;
-        timer.on = g_pass_profiling;
-        cudaEvent_t e0, e1;
-        LDS_CUDA(cudaEventCreate(&e0));
-        LDS_CUDA(cudaEventCreate(&e1));
-        struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } evg{e0, e1};
-
-        DevBuf<double> r_int(std::max(n, 1), s), r_orig(std::max(n, 1), s);
-        DevBuf<int64_t> R_int(std::max(n, 1), s), R_orig(std::max(n, 1), s);
-        const int64_t Dn = (int64_t)(iters + 1) * (iters + 2) * (d == LDS_TRIANGLE ? 3 : 1);
-        out->D = Dn;
-
-        if (d == LDS_EDGE) {
-            EdgeFwOut fo;
-            LDS_CUDA(cudaEventRecord(e0, s));
-            bool fast = g_fw_variant != 1 &&
-                        run_edge_fw_oriented(g, iters, p, out->W != nullptr, out->last != nullptr, fo, timer);
-            if (fast) {
-                LDS_CUDA(cudaEventRecord(e1, s));
-                g->pass_bytes = 4 * g->m + 8 * ((g->m + 31) / 32) + 4 * g->fwv_nz +
-                                (std::string(g->pass_kernel) == "fw_opass32_kernel" ? 4 : 8) * (int64_t)nact;
-                if (out->r) {
-                    to_original_order_f64(g, fo.r_int.get(), r_orig.get());
-                    copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
-                }
-                if (out->R) {
-                    to_original_order_i64(g, fo.R_int.get(), R_orig.get());
-                    copy_out(out->R, where, R_orig.get(), n * sizeof(int64_t), s);
-                }
-                if (out->W && g->m) copy_out(out->W, where, fo.W_edge.get(), g->m * sizeof(int64_t), s);
-                if (out->last && g->m) copy_out(out->last, where, fo.last_edge.get(), g->m, s);
-                LDS_CUDA(cudaStreamSynchronize(s));
-            } else {
-            EdgeFwState st;
-            run_edge_fw(g, iters, p, st, timer);
-            LDS_CUDA(cudaEventRecord(e1, s));
-            {
-                const int64_t ns = 2 * g->m, nc = (ns + 31) / 32;
-                if (p == LDS_FP64) {
-                    g->pass_kernel = "fw64_slot_kernel";
-                    g->pass_bytes = 4 * ns + 4 * nc + 4 * nc + 16 * ns + 8 * (int64_t)nact;
-                } else {
-                    g->pass_kernel = "fw_edge_pass_kernel";
-                    g->pass_bytes = 4 * ns + 8 * nc + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
-                }
-            }
-            const int64_t nslots = 2 * g->m;
-            // exact loads of the returned weights
-            if (nact) LDS_LAUNCH(loads_from_slots_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), st.W.get(), nact, R_int.get());
-            if (n > nact) LDS_LAUNCH(pad_i64_kernel, grid_for(n - nact, blk), blk, 0, s, R_int.get(), nact, n);
-            if (out->r) {
-                if (p == LDS_EXACT)
-                    LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
-                else if (p == LDS_FP32)
-                    LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
-                else
-                    LDS_LAUNCH(loads_to_double_kernel<double>, grid_for(n, blk), blk, 0, s, st.r64.get(), nact, n, 1.0, r_int.get());
-                to_original_order_f64(g, r_int.get(), r_orig.get());
-                copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
-            }
-            if (out->R) {
-                to_original_order_i64(g, R_int.get(), R_orig.get());
-                copy_out(out->R, where, R_orig.get(), n * sizeof(int64_t), s);
-            }
-            if ((out->W || out->last) && g->m) {
-                DevBuf<int64_t> Wd(out->W ? g->m : 0, s);
-                DevBuf<uint8_t> Ld(out->last ? g->m : 0, s);
-                const uint32_t* lastp = st.planes.get() + std::max<int64_t>(st.last_plane, 0) * ((nslots + 31) / 32);
-                LDS_LAUNCH(edge_weights_kernel, grid_for(g->m, blk), blk, 0, s, g->rowptr.get(), g->col.get(), g->eu.get(),
-                           g->ev.get(), g->m, st.W.get(), lastp, Wd.get(), Ld.get());
-                if (out->W) copy_out(out->W, where, Wd.get(), g->m * sizeof(int64_t), s);
-                if (out->last) {
-                    if (iters == 0) LDS_CUDA(cudaMemsetAsync(Ld.get(), 0, g->m, s));
-                    copy_out(out->last, where, Ld.get(), g->m, s);
-                }
-                LDS_CUDA(cudaStreamSynchronize(s));
-            }
-            }
-        } else {
-            ensure_triangles(g);
-            TriFwState st;
-            LDS_CUDA(cudaEventRecord(e0, s));
-            run_tri_fw(g, iters, p, st, timer);
-            LDS_CUDA(cudaEventRecord(e1, s));
-            g->pass_kernel = "fw_tri_pass_kernel";
-            g->pass_bytes = 12 * g->ntri + 8 * ((g->ntri + 31) / 32) + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
-            const int64_t ntri = g->ntri;
-            LDS_CUDA(cudaMemsetAsync(R_int.get(), 0, std::max(n, 1) * sizeof(int64_t), s));
-            if (ntri) LDS_LAUNCH(tri_loads_from_w_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
-                                                                                   st.W.get(), (unsigned long long*)R_int.get());
-            LDS_CHECK_LAUNCH();
-            if (out->r) {
-                if (p == LDS_EXACT)
-                    LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
-                else
-                    LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
-                LDS_CHECK_LAUNCH();
-                to_original_order_f64(g, r_int.get(), r_orig.get());
-                copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
-            }
-            if (out->R) {
-                to_original_order_i64(g, R_int.get(), R_orig.get());
-                copy_out(out->R, where, R_orig.get(), n * sizeof(int64_t), s);
-            }
-            if (out->W && ntri) {
-                DevBuf<int64_t> Wd(3 * ntri, s);
-                LDS_LAUNCH(widen_u32_kernel, grid_for(3 * ntri, blk), blk, 0, s, st.W.get(), 3 * ntri, Wd.get());
-                LDS_CHECK_LAUNCH();
-                copy_out(out->W, where, Wd.get(), 3 * ntri * sizeof(int64_t), s);
-                LDS_CUDA(cudaStreamSynchronize(s));
-            }
-            if (out->last && ntri) {
-                DevBuf<uint8_t> Ld(ntri, s);
-                int64_t nch = (ntri + 31) / 32;
-                const uint32_t* p0 = st.planes.get() + 2 * std::max<int64_t>(st.last_pair, 0) * nch;
-                if (iters == 0) LDS_CUDA(cudaMemsetAsync(Ld.get(), 2, ntri, s));
-                else LDS_LAUNCH(tri_last_kernel, grid_for(ntri, blk), blk, 0, s, p0, p0 + nch, ntri, Ld.get());
-                LDS_CHECK_LAUNCH();
-                copy_out(out->last, where, Ld.get(), ntri, s);
-                LDS_CUDA(cudaStreamSynchronize(s));
-            }
+        const int32_t n = g->n;
+        out->D = g->fw_D;
+        if (out->r && n) {
+            DevBuf<double> r_orig(n, s);
+            to_original_order_f64(g, g->fw_r.get(), r_orig.get());
+            copy_out(out->r, where, r_orig.get(), n * sizeof(double), s);
+            LDS_CUDA(cudaStreamSynchronize(s));
         }
+        if (out->R && n) {
+            DevBuf<int64_t> R_orig(n, s);
+            to_original_order_i64(g, g->fw_R.get(), R_orig.get());
+            copy_out(out->R, where, R_orig.get(), n * sizeof(int64_t), s);
+            LDS_CUDA(cudaStreamSynchronize(s));
+        }
+        const int64_t npat = d == LDS_EDGE ? g->m : g->ntri;
+        if (out->W && npat) copy_out(out->W, where, g->fw_W.get(), (d == LDS_EDGE ? 1 : 3) * npat * sizeof(int64_t), s);
+        if (out->last && npat) copy_out(out->last, where, g->fw_last.get(), npat, s);
         LDS_CUDA(cudaStreamSynchronize(s));
-        float ms = 0;
-        LDS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        g->fw_ms = ms;
-        g->pass_launches = timer.used / 2;
-        g->pass_us = timer.used ? 1000.0 * timer.total_ms() / (timer.used / 2) : 0.0;
     });
 }
 

@@ -28,6 +28,9 @@ struct lds_graph {
     // triangles (lazy): internal ids a < b < c, triangle order
     int64_t ntri = -1;
     lds::DevBuf<int32_t> ta, tb, tc;
+    // vertex -> triangle incidence (lazy): triangles of x at vt_idx[vt_ptr[x] .. vt_ptr[x+1]), ascending
+    lds::DevBuf<int64_t> vt_ptr;      // [nact + 1]
+    lds::DevBuf<int32_t> vt_idx;      // [3 |T|]
 
     // FW view: vertices relabelled by (degree descending, id ascending); every
     // edge stored once, in the row of its lower-ranked endpoint, pointing to the
@@ -43,6 +46,16 @@ struct lds_graph {
     lds::DevBuf<int64_t> fwv_edge;     // [m] canonical edge id of each slot
     lds::DevBuf<int32_t> fwv_ta, fwv_tb, fwv_tc;  // triangles in fw ids (lazy)
 
+    // state of the most recent Frank-Wolfe run (internal ids), read by the later stages
+    bool fw_valid = false;
+    lds_density fw_density = LDS_EDGE;
+    int32_t fw_iters = 0;
+    int64_t fw_D = 0;
+    lds::DevBuf<int64_t> fw_R;        // [n] exact loads of the weights below (R = D r)
+    lds::DevBuf<double> fw_r;         // [n] reported loads
+    lds::DevBuf<int64_t> fw_W;        // [m] D alpha_{u,v} per canonical edge, or [3 |T|] per triangle row
+    lds::DevBuf<uint8_t> fw_last;     // [m] or [|T|] last-iteration choices
+
     // timing of the most recent lds_fw
     double fw_ms = 0.0, pass_us = 0.0;
     int64_t pass_launches = 0;
@@ -55,8 +68,14 @@ namespace lds {
 // Builds slot_edge (canonical edge id of every CSR slot) if not present.
 void ensure_slot_edge(lds_graph* g);
 
+// Runs `iters` Frank-Wolfe iterations and leaves the results in g->fw_*.
+void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool want_last);
+
 // Builds the FW view (see lds_graph) if not present.
 void ensure_fw_view(lds_graph* g);
+
+// Builds the vertex -> triangle incidence (ascending triangle order) if not present.
+void ensure_vertex_triangles(lds_graph* g);
 
 // Lists triangles into g->ta/tb/tc if not present.
 void ensure_triangles(lds_graph* g);

@@ -79,6 +79,8 @@ def load():
     _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
     _sig(lib, "lds_launch_count", i64, [])
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
+    _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
+                                               ctypes.POINTER(i32), P])
     _lib = lib
     return lib
 
@@ -222,6 +224,29 @@ class Graph:
                              ctypes.byref(res)))
         out["D"] = int(res.D)
         return out
+
+    def extract_sg(self):
+        """Stable groups (Alg. 2) of the last fw() run on this graph.  Returns a
+        dict: order (vertices by load, original ids), groups (list of vertex
+        arrays, top first), remainder (vertices after the last group),
+        intervals (list of (lo_num, hi_num) over D), D and cuts (1-based)."""
+        n = self.n
+        order = np.empty(max(n, 1), dtype=np.int32)
+        gend = np.empty(max(n, 1), dtype=np.int64)
+        lo = np.empty(max(n, 1), dtype=np.int64)
+        hi = np.empty(max(n, 1), dtype=np.int64)
+        cuts = np.empty(max(n, 1), dtype=np.int64)
+        ng, nc, D = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().lds_extract_sg(self._h, _ptr(order), ctypes.byref(ng), _ptr(gend), _ptr(lo), _ptr(hi),
+                                     ctypes.byref(D), ctypes.byref(nc), _ptr(cuts)))
+        order = order[:n]
+        groups, start = [], 0
+        for k in range(ng.value):
+            groups.append(order[start:gend[k]])
+            start = int(gend[k])
+        return {"order": order, "groups": groups, "remainder": order[start:],
+                "intervals": list(zip(lo[:ng.value].tolist(), hi[:ng.value].tolist())),
+                "D": int(D.value), "cuts": cuts[:nc.value].tolist()}
 
     def fw_timing(self):
         a, b, c, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()

@@ -1,0 +1,73 @@
+"""GPU parity of the stages after Frank-Wolfe (ExtractSG, Pruning, the
+verification flows and the top-k driver) against the CPU oracle.  Every
+quantity here is exact (integers and rationals), so the bar is bit-exactness."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import extract_sg as osg
+from oracle import fw as ofw
+from oracle import graph as ograph
+from paper_2504_10937_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lds():
+    from paper_2504_10937_gb300 import lds as _l
+    _l.load()
+    return _l
+
+
+def _graphs():
+    out = []
+    out.append(synth.gnp_planted(40, 0.15, (7, 6), (0.9, 0.8), seed=21)[:3])
+    out.append(synth.gnp_planted(300, 0.02, (15, 10, 8), (0.9, 0.7, 0.95), seed=22)[:3])
+    out.append(synth.chung_lu(3000, 12000, 2.1, seed=23, n_blocks=4, block_size_range=(15, 50))[:3])
+    out.append(synth.rmat(10, 6, 0.57, 0.19, 0.19, seed=24, n_cliques=3, clique_size_range=(10, 25))[:3])
+    return out
+
+
+def _ir(n, u, v, tris=None):
+    if tris is None:
+        core = ograph.core_numbers(n, u, v)
+        div = 2
+    else:
+        core = ograph.tr_core_numbers(n, tris)
+        div = 3
+    return ({x: Fraction(int(core[x])) for x in range(n)}, {x: Fraction(int(core[x]), div) for x in range(n)})
+
+
+@pytest.mark.parametrize("N", [2, 30, 250])
+def test_extract_sg_edge_matches_oracle(lds, N):
+    for n, u, v in _graphs():
+        with lds.Graph(n, u, v) as g:
+            g.fw(N, precision="exact", want=())
+            got = g.extract_sg()
+        R, W, Dn, _ = ofw.fw_edge_exact(n, u, v, N)
+        ub, lb = _ir(n, u, v)
+        want = osg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+        assert got["D"] == Dn
+        assert got["order"].tolist() == want["order"]
+        assert got["cuts"] == want["cuts"]
+        assert [sorted(x.tolist()) for x in got["groups"]] == [sorted(x) for x in want["groups"]]
+        assert [Fraction(lo, Dn) for lo, _ in got["intervals"]] == [lo for lo, _ in want["intervals"]]
+        assert [Fraction(hi, Dn) for _, hi in got["intervals"]] == [hi for _, hi in want["intervals"]]
+
+
+@pytest.mark.parametrize("N", [2, 40])
+def test_extract_sg_triangle_matches_oracle(lds, N):
+    for n, u, v in _graphs():
+        tris = ograph.triangles(n, u, v)
+        with lds.Graph(n, u, v) as g:
+            g.fw(N, density="triangle", precision="exact", want=())
+            got = g.extract_sg()
+        R, W, Dn3, _ = ofw.fw_tri_exact(n, tris, N)
+        ub, lb = _ir(n, u, v, tris)
+        want = osg.extract_sg_tri(range(n), tris, W, Dn3, ub, lb)
+        assert got["order"].tolist() == want["order"]
+        assert got["cuts"] == want["cuts"]
+        assert [sorted(x.tolist()) for x in got["groups"]] == [sorted(x) for x in want["groups"]]
+        assert [(Fraction(lo, Dn3), Fraction(hi, Dn3)) for lo, hi in got["intervals"]] == want["intervals"]
