@@ -168,6 +168,17 @@ lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us
 lds_status lds_extract_sg(lds_graph* g, int32_t* order, int32_t* ngroups, int64_t* group_end, int64_t* lo_num,
                           int64_t* hi_num, int64_t* D, int32_t* ncuts, int64_t* cuts);
 
+/* Pruning (Alg. 3) of this graph with the given bounds on the compact numbers.
+ * Pruning rule 1 (Cor. 1) removes every vertex x with an edge (x, y) such that
+ * ub(x) < lb(y); Pruning rule 2 (Lemma 5, Lemma 6) then removes vertices whose
+ * core number (tr-core number for LDS_TRIANGLE) in the remaining graph is below
+ * lb, until none is left.
+ *   ub_num, ub_den, lb_num, lb_den  host int64[n]: bounds num / den (den > 0)
+ *   status  host uint8[n] output: 0 kept, 1 removed by rule 1, 2 by rule 2
+ * Errors: LDS_EINVAL, LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_prune(lds_graph* g, lds_density d, const int64_t* ub_num, const int64_t* ub_den,
+                     const int64_t* lb_num, const int64_t* lb_den, uint8_t* status);
+
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load

@@ -77,6 +77,9 @@ void ensure_fw_view(lds_graph* g);
 // Builds the vertex -> triangle incidence (ascending triangle order) if not present.
 void ensure_vertex_triangles(lds_graph* g);
 
+// Core (tr-core) numbers of G[alive] (internal ids, -1 outside the mask).
+void core_numbers(lds_graph* g, bool tri, int64_t* core_int, const uint8_t* init_alive);
+
 // Lists triangles into g->ta/tb/tc if not present.
 void ensure_triangles(lds_graph* g);
 

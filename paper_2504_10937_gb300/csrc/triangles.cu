@@ -198,6 +198,46 @@ __global__ void vt_fill_kernel(const int32_t* ta, const int32_t* tb, const int32
     }
 }
 
+__global__ void alive_init_kernel(const uint8_t* init, int32_t nact, uint8_t* alive, int64_t* core, int32_t* nalive) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t c = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
+        uint8_t a = init ? (init[x] ? 1 : 0) : 1;
+        alive[x] = a;
+        core[x] = -1;
+        c += a;
+    }
+    if (c) atomicAdd(nalive, c);
+}
+
+__global__ void alive_degree_kernel(const int64_t* rowptr, const int32_t* col, const uint8_t* alive, int32_t nact,
+                                    int32_t* deg) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
+        if (!alive[x]) continue;
+        int32_t d = 0;
+        for (int64_t q = rowptr[x], e = rowptr[x + 1]; q < e; ++q) d += alive[col[q]];
+        deg[x] = d;
+    }
+}
+
+// triangle counts of G[alive]; triangles with a dead vertex are marked dead
+__global__ void alive_tri_count_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
+                                       const uint8_t* alive, int32_t* deg, uint8_t* tdead) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        int32_t a = ta[t], b = tb[t], c = tc[t];
+        if (alive[a] && alive[b] && alive[c]) {
+            atomicAdd(deg + a, 1);
+            atomicAdd(deg + b, 1);
+            atomicAdd(deg + c, 1);
+        } else {
+            unsigned int* word = (unsigned int*)(tdead + (t & ~3ll));
+            atomicOr(word, 1u << (8 * (t & 3)));
+        }
+    }
+}
+
 __global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < to; x += stride) p[x] = v;
@@ -261,8 +301,9 @@ void ensure_triangles(lds_graph* g) {
     g->info.triangles = ntri;
 }
 
-// core numbers in internal ids: core_int[nact]
-static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int) {
+// Core (tr-core) numbers of G[alive] in internal ids: core_int[nact]; vertices
+// outside `init_alive` (device mask, NULL = every vertex) get -1.
+static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, const uint8_t* init_alive) {
     cudaStream_t s = g->stream;
     const int32_t nact = g->nact;
     const int blk = 256;
@@ -270,43 +311,34 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int) {
     DevBuf<int32_t> deg(nact, s), frontier(nact, s), fcount(1, s);
     DevBuf<uint8_t> alive(nact, s);
     DevBuf<int64_t> minalive(1, s);
-    LDS_CUDA(cudaMemsetAsync(alive.get(), 1, nact, s));
-    DevBuf<int64_t> vptr;
-    DevBuf<int32_t> vtri;
+    DevBuf<int32_t> nalive(1, s);
+    LDS_CUDA(cudaMemsetAsync(nalive.get(), 0, sizeof(int32_t), s));
+    LDS_LAUNCH(alive_init_kernel, grid_for(nact, blk), blk, 0, s, init_alive, nact, alive.get(), core_int, nalive.get());
     DevBuf<uint8_t> tdead;
+    LDS_CUDA(cudaMemsetAsync(deg.get(), 0, nact * sizeof(int32_t), s));
     if (!tri) {
-        LDS_LAUNCH(degree_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), nact, deg.get());
-        LDS_CHECK_LAUNCH();
+        LDS_LAUNCH(alive_degree_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), g->col.get(), alive.get(), nact,
+                   deg.get());
     } else {
-        ensure_triangles(g);
+        ensure_vertex_triangles(g);
         const int64_t ntri = g->ntri;
-        LDS_CUDA(cudaMemsetAsync(deg.get(), 0, nact * sizeof(int32_t), s));
-        if (ntri) LDS_LAUNCH(vt_count_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri, deg.get());
-        LDS_CHECK_LAUNCH();
-        vptr.alloc(nact + 1, s);
-        DevBuf<int32_t> deg1(nact + 1, s);
-        LDS_CUDA(cudaMemsetAsync(deg1.get(), 0, (nact + 1) * sizeof(int32_t), s));
-        LDS_CUDA(cudaMemcpyAsync(deg1.get(), deg.get(), nact * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        exclusive_scan_i32_to_i64(deg1.get(), vptr.get(), nact + 1, s);
-        vtri.alloc(std::max<int64_t>(3 * ntri, 1), s);
-        DevBuf<int32_t> cursor(nact, s);
-        LDS_CUDA(cudaMemsetAsync(cursor.get(), 0, nact * sizeof(int32_t), s));
-        if (ntri) LDS_LAUNCH(vt_fill_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri, vptr.get(),
-                                                                     cursor.get(), vtri.get());
-        LDS_CHECK_LAUNCH();
         tdead.alloc(((ntri + 3) & ~3ll) + 4, s);
         LDS_CUDA(cudaMemsetAsync(tdead.get(), 0, ((ntri + 3) & ~3ll) + 4, s));
+        if (ntri)
+            LDS_LAUNCH(alive_tri_count_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
+                       alive.get(), deg.get(), tdead.get());
     }
+    int32_t remaining = 0;
+    LDS_CUDA(cudaMemcpyAsync(&remaining, nalive.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
     int64_t k = 0;
-    int32_t remaining = nact;
     int64_t guard_steps = 0;
     while (remaining > 0) {
         LDS_CUDA(cudaMemsetAsync(fcount.get(), 0, sizeof(int32_t), s));
         int64_t big = INT64_MAX;
         LDS_CUDA(cudaMemcpyAsync(minalive.get(), &big, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        LDS_LAUNCH(peel_select_kernel, grid_for(nact, blk), blk, 0, s, deg.get(), alive.get(), nact, k, core_int, frontier.get(),
-                                                               fcount.get(), minalive.get());
-        LDS_CHECK_LAUNCH();
+        LDS_LAUNCH(peel_select_kernel, grid_for(nact, blk), blk, 0, s, deg.get(), alive.get(), nact, k, core_int,
+                   frontier.get(), fcount.get(), minalive.get());
         int32_t hf = 0;
         int64_t hmin = 0;
         LDS_CUDA(cudaMemcpyAsync(&hf, fcount.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -320,17 +352,17 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int) {
         remaining -= hf;
         if (!tri)
             LDS_LAUNCH(peel_edges_kernel, grid_for(hf, 128), 128, 0, s, g->rowptr.get(), g->col.get(), frontier.get(), hf,
-                                                                alive.get(), deg.get());
+                       alive.get(), deg.get());
         else
-            LDS_LAUNCH(peel_tris_kernel, grid_for(hf, 128), 128, 0, s, vptr.get(), vtri.get(), frontier.get(), hf, g->ta.get(),
-                                                               g->tb.get(), g->tc.get(), tdead.get(), alive.get(),
-                                                               deg.get());
-        LDS_CHECK_LAUNCH();
+            LDS_LAUNCH(peel_tris_kernel, grid_for(hf, 128), 128, 0, s, g->vt_ptr.get(), g->vt_idx.get(), frontier.get(),
+                       hf, g->ta.get(), g->tb.get(), g->tc.get(), tdead.get(), alive.get(), deg.get());
         LDS_REQUIRE(++guard_steps < 4 * (int64_t)nact + 16, LDS_ETIMEOUT, "core numbers: peeling did not finish");
     }
 }
 
-void core_numbers(lds_graph* g, bool tri, int64_t* core_int_out) { core_numbers_internal(g, tri, core_int_out); }
+void core_numbers(lds_graph* g, bool tri, int64_t* core_int_out, const uint8_t* init_alive) {
+    core_numbers_internal(g, tri, core_int_out, init_alive);
+}
 
 }  // namespace lds
 
@@ -370,7 +402,7 @@ lds_status lds_core_numbers(lds_graph* g, lds_density d, int64_t* core, lds_mem 
         if (n == 0) return;
         DevBuf<int64_t> ci(n, s), co(n, s);
         LDS_CUDA(cudaMemsetAsync(ci.get(), 0, n * sizeof(int64_t), s));
-        core_numbers_internal(g, d == LDS_TRIANGLE, ci.get());
+        core_numbers_internal(g, d == LDS_TRIANGLE, ci.get(), nullptr);
         to_original_order_i64(g, ci.get(), co.get());
         copy_out(core, where, co.get(), n * sizeof(int64_t), s);
         LDS_CUDA(cudaStreamSynchronize(s));

@@ -79,6 +79,7 @@ def load():
     _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
     _sig(lib, "lds_launch_count", i64, [])
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
+    _sig(lib, "lds_prune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
                                                ctypes.POINTER(i32), P])
     _lib = lib
@@ -247,6 +248,21 @@ class Graph:
         return {"order": order, "groups": groups, "remainder": order[start:],
                 "intervals": list(zip(lo[:ng.value].tolist(), hi[:ng.value].tolist())),
                 "D": int(D.value), "cuts": cuts[:nc.value].tolist()}
+
+    def prune(self, ub, lb, density: str = "edge"):
+        """Alg. 3 with bounds given as sequences of fractions.Fraction (or ints)
+        indexed by vertex.  Returns uint8[n]: 0 kept, 1 rule 1, 2 rule 2."""
+        from fractions import Fraction
+        n = self.n
+        arrs = []
+        for b in (ub, lb):
+            fr = [Fraction(x) for x in b]
+            arrs.append(np.array([f.numerator for f in fr], dtype=np.int64))
+            arrs.append(np.array([f.denominator for f in fr], dtype=np.int64))
+        st = np.empty(max(n, 1), dtype=np.uint8)
+        _check(load().lds_prune(self._h, DENSITY[density], _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                                _ptr(arrs[3]), _ptr(st)))
+        return st[:n]
 
     def fw_timing(self):
         a, b, c, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()

@@ -71,3 +71,43 @@ def test_extract_sg_triangle_matches_oracle(lds, N):
         assert got["cuts"] == want["cuts"]
         assert [sorted(x.tolist()) for x in got["groups"]] == [sorted(x) for x in want["groups"]]
         assert [(Fraction(lo, Dn3), Fraction(hi, Dn3)) for lo, hi in got["intervals"]] == want["intervals"]
+
+
+def _oracle_prune(n, u, v, ub, lb, tris=None):
+    from oracle import prune as oprune
+    kept, groups, r1, r2 = oprune.prune(n, u, v, range(n), [], ub, lb, tris=tris)
+    st = np.zeros(n, np.uint8)
+    st[sorted(r1)] = 1
+    st[sorted(r2)] = 2
+    return st
+
+
+@pytest.mark.parametrize("N", [3, 60])
+@pytest.mark.parametrize("triangle", [False, True])
+def test_prune_matches_oracle(lds, N, triangle):
+    for n, u, v in _graphs():
+        tris = ograph.triangles(n, u, v) if triangle else None
+        ub, lb = _ir(n, u, v, tris)
+        if triangle:
+            R, W, Dn, _ = ofw.fw_tri_exact(n, tris, N)
+            res = osg.extract_sg_tri(range(n), tris, W, Dn, ub, lb)
+        else:
+            R, W, Dn, _ = ofw.fw_edge_exact(n, u, v, N)
+            res = osg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+        ub2 = [res["ub"][x] for x in range(n)]
+        lb2 = [res["lb"][x] for x in range(n)]
+        with lds.Graph(n, u, v) as g:
+            got = g.prune(ub2, lb2, "triangle" if triangle else "edge")
+        assert np.array_equal(got, _oracle_prune(n, u, v, res["ub"], res["lb"], tris))
+
+
+def test_prune_fig1_example(lds):
+    from helpers import load_expected, load_graph, parse_ids
+    from oracle import decomp
+    n, u, v = load_graph("fig1_graph.txt")
+    exp = load_expected("fig1_expected.txt")
+    phi = decomp.compact_numbers(n, list(zip(u.tolist(), v.tolist())))
+    with lds.Graph(n, u.astype(np.int32), v.astype(np.int32)) as g:
+        st = g.prune([phi[x] for x in range(n)], [phi[x] for x in range(n)])
+    assert sorted(np.nonzero(st == 1)[0].tolist()) == parse_ids(exp["pruned_rule1"])
+    assert sorted(np.nonzero(st == 2)[0].tolist()) == parse_ids(exp["pruned_rule2"])
