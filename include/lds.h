@@ -179,6 +179,21 @@ lds_status lds_extract_sg(lds_graph* g, int32_t* order, int32_t* ngroups, int64_
 lds_status lds_prune(lds_graph* g, lds_density d, const int64_t* ub_num, const int64_t* ub_den,
                      const int64_t* lb_num, const int64_t* lb_den, uint8_t* status);
 
+/* Maximum flow of the pattern network of Alg. 8: a source, one node per
+ * pattern, one node per vertex, a sink; arcs source -> pattern (capacity q),
+ * pattern -> each of its vertices (q), vertex -> sink (p), i.e. rho = p / q
+ * scaled by q.  GPU push-relabel.
+ *   nv, np            vertices and patterns
+ *   pat_ptr[np + 1], pat_idx[pat_ptr[np]]  host arrays: pattern j lists vertices
+ *                     pat_idx[pat_ptr[j] .. pat_ptr[j+1]) (indices in [0, nv))
+ *   flow              output: maximum flow value
+ *   source_side[nv]   output (may be NULL): 1 for vertices on the largest source
+ *                     side of a minimum cut (those that cannot reach the sink in
+ *                     the final residual network; Lemma 9's cut)
+ * Errors: LDS_EINVAL, LDS_ETIMEOUT (iteration bound), LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_pattern_max_flow(int32_t nv, int32_t np, const int64_t* pat_ptr, const int32_t* pat_idx, int64_t p,
+                                int64_t q, int64_t* flow, uint8_t* source_side);
+
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load

@@ -79,6 +79,7 @@ def load():
     _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
     _sig(lib, "lds_launch_count", i64, [])
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
+    _sig(lib, "lds_pattern_max_flow", ctypes.c_int, [i32, i32, P, P, i64, i64, ctypes.POINTER(i64), P])
     _sig(lib, "lds_prune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
                                                ctypes.POINTER(i32), P])
@@ -126,6 +127,22 @@ def launch_count() -> int:
 
 def debug_fail_alloc_after(k: int):
     load().lds_debug_fail_alloc_after(int(k))
+
+
+def pattern_max_flow(nv: int, patterns, p: int, q: int):
+    """Alg. 8's network over vertices 0..nv-1 and the given patterns (sequences
+    of vertex indices).  Returns (flow, source_side uint8[nv])."""
+    ptr = np.zeros(len(patterns) + 1, dtype=np.int64)
+    for j, pat in enumerate(patterns):
+        ptr[j + 1] = ptr[j] + len(pat)
+    idx = np.array([x for pat in patterns for x in pat], dtype=np.int32)
+    if idx.size == 0:
+        idx = np.zeros(1, dtype=np.int32)
+    side = np.zeros(max(nv, 1), dtype=np.uint8)
+    f = ctypes.c_int64()
+    _check(load().lds_pattern_max_flow(int(nv), len(patterns), _ptr(ptr), _ptr(idx), int(p), int(q),
+                                       ctypes.byref(f), _ptr(side)))
+    return int(f.value), side[:nv]
 
 
 class Graph:

@@ -111,3 +111,38 @@ def test_prune_fig1_example(lds):
         st = g.prune([phi[x] for x in range(n)], [phi[x] for x in range(n)])
     assert sorted(np.nonzero(st == 1)[0].tolist()) == parse_ids(exp["pruned_rule1"])
     assert sorted(np.nonzero(st == 2)[0].tolist()) == parse_ids(exp["pruned_rule2"])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_pattern_max_flow_matches_dinic(lds, seed):
+    from oracle import verify as over
+    rng = synth.SplitMix64(70000 + seed)
+    nv = int(rng.integers(1, 40, 1)[0])
+    npat = int(rng.integers(0, 80, 1)[0])
+    pats = []
+    for _ in range(npat):
+        k = int(rng.integers(1, 4, 1)[0])
+        pats.append(tuple(sorted(set(rng.integers(0, nv, k).tolist()))))
+    p = int(rng.integers(1, 9, 1)[0])
+    q = int(rng.integers(1, 5, 1)[0])
+    flow, side = lds.pattern_max_flow(nv, pats, p, q)
+    rho = Fraction(p, q)
+    net, s, t, node = over.pattern_network(range(nv), pats, rho)
+    # pattern_network scales by rho's reduced form; compare flows in the same units
+    want = net.max_flow(s, t)
+    scale = Fraction(q, rho.denominator)
+    assert Fraction(flow) == want * scale
+    side_want = set(net.maximal_source_side(t))
+    assert [int(node[x] in side_want) for x in range(nv)] == side.tolist()
+
+
+def test_pattern_max_flow_larger_network(lds):
+    from oracle import verify as over
+    n, u, v, _ = synth.chung_lu(400, 2400, 2.1, seed=71, n_blocks=2, block_size_range=(20, 30))
+    pats = list(zip(u.tolist(), v.tolist())) + [(x,) for x in range(0, n, 7)]
+    for rho in (Fraction(3, 1), Fraction(7, 2), Fraction(11, 4)):
+        flow, side = lds.pattern_max_flow(n, pats, rho.numerator, rho.denominator)
+        net, s, t, node = over.pattern_network(range(n), pats, rho)
+        assert flow == net.max_flow(s, t)
+        sw = set(net.maximal_source_side(t))
+        assert [int(node[x] in sw) for x in range(n)] == side.tolist()
