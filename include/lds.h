@@ -194,6 +194,46 @@ lds_status lds_prune(lds_graph* g, lds_density d, const int64_t* ub_num, const i
 lds_status lds_pattern_max_flow(int32_t nv, int32_t np, const int64_t* pat_ptr, const int32_t* pat_idx, int64_t p,
                                 int64_t q, int64_t* flow, uint8_t* source_side);
 
+/* Result of lds_topk, owned by the library until lds_result_free. */
+typedef struct {
+    int32_t  count;         /* number of sets (<= k)                                    */
+    int64_t* dens_num;      /* [count] density of set i = dens_num[i] / dens_den[i],     */
+    int64_t* dens_den;      /*         as a reduced fraction                              */
+    int64_t* offsets;       /* [count + 1] set i is vertices[offsets[i] .. offsets[i+1])  */
+    int32_t* vertices;      /* original ids, ascending within each set                   */
+} lds_result;
+
+/* Counters and phase times of the most recent lds_topk on this thread. */
+typedef struct {
+    int64_t fw_rounds;          /* Frank-Wolfe runs (first round + refinements)      */
+    int64_t fw_edge_updates;    /* sum over runs of |E'| (|T'|) x iterations         */
+    int64_t certified;          /* components that passed IsLDS / IsLTDS             */
+    int64_t failed;             /* self-densest components that failed it            */
+    int64_t refined;            /* refinement rounds on G[C]                         */
+    int64_t exact_settled;      /* components settled by exact compact numbers       */
+    int64_t skipped_by_bound;   /* groups skipped since ub < k-th density            */
+    int64_t flows;              /* maximum-flow runs in verification                 */
+    int64_t denser_neighbour;   /* candidates rejected by a denser neighbour         */
+    double ms_total, ms_fw, ms_extract, ms_prune, ms_verify;
+} lds_topk_stats_t;
+
+/* Top-k locally densest subgraphs (Problem 1; LDScvx, Alg. 5) for LDS_EDGE, or
+ * top-k locally triangle-densest subgraphs (Problem 2; LTDScvx, Sec. 6) for
+ * LDS_TRIANGLE.  The answer is the k sets of largest density among all LDSs
+ * (LTDSs) of positive density, densest first, ties by smallest member id; every
+ * returned set is certified by IsDensest and IsLDS / IsLTDS (max-flow), and the
+ * search continues until no unexamined vertex can belong to a denser one, so
+ * the answer does not depend on `iters` or the arithmetic.
+ *   iters   Frank-Wolfe iterations per round (refinements may use up to 8x)
+ *   p       arithmetic of the iterations (lds_precision)
+ *   out     receives the result; free with lds_result_free
+ * Errors: LDS_EINVAL, LDS_ENOMEM, LDS_ETIMEOUT, LDS_EOVERFLOW, LDS_ECUDA. */
+lds_status lds_topk(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, lds_result** out);
+
+void lds_result_free(lds_result* r);
+
+lds_status lds_topk_last_stats(lds_topk_stats_t* stats);
+
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load

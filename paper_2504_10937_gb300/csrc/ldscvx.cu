@@ -1,0 +1,633 @@
+// The LDScvx / LTDScvx driver (Alg. 5 and its triangle extension, Sec. 6)
+// orchestrated on the host; every step over vertices, edges, triangles or flow
+// networks runs in the library's kernels.
+//
+// Readings (the same as the CPU oracle's driver):
+//   * Initial reduction: ub = core number, lb = core / 2 (tr-core, tr-core / 3).
+//   * The first round (FW, ExtractSG, Pruning) runs on G itself, so its bounds
+//     hold for G.  Refinement rounds run on G[C] for a component C of a group:
+//     their lower bounds are lifted to G, their upper bounds stay in the round.
+//   * Every popped group is split into connected components.  A component that
+//     is self-densest is certified by IsLDS / IsLTDS on G (or dropped); one that
+//     is not is refined.  A refinement that returns the component unchanged is
+//     retried with 2N, 4N, 8N iterations and then settled exactly (compact
+//     numbers of G[C] by repeated flows, LDSs of G[C] by their level sets, each
+//     certified on G).
+//   * Completeness: every group is processed, except that once k sets are
+//     certified a group whose vertices all have ub < rho_k is skipped.
+//   * Output: density descending, ties by smallest member id.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "extract_sg.cuh"
+#include "flow.cuh"
+#include "prims.cuh"
+#include "prune.cuh"
+#include "verify.cuh"
+
+namespace lds {
+
+namespace {
+
+typedef __int128 i128;
+constexpr int DB = 256;
+
+__global__ void init_bounds_kernel(const int64_t* core, int32_t nact, int32_t n, int64_t div, int64_t* un, int64_t* ud,
+                                   int64_t* ln, int64_t* ld) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        int64_t c = x < nact ? core[x] : 0;
+        un[x] = c;
+        ud[x] = 1;
+        ln[x] = c;
+        ld[x] = div;
+    }
+}
+
+// a/b reduced to lowest terms is not needed: comparisons cross-multiply
+__device__ __forceinline__ bool fr_lt(int64_t a, int64_t b, int64_t c, int64_t d) {
+    return (i128)a * d < (i128)c * b;
+}
+
+// tighten the bounds of the vertices of every accepted group
+__global__ void apply_groups_kernel(const int32_t* order, const int64_t* gend, const int64_t* lo, const int64_t* hi,
+                                    int32_t ng, int64_t Dn, int64_t npos, int64_t* un, int64_t* ud, int64_t* ln,
+                                    int64_t* ld) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += stride) {
+        int lo_i = 0, hi_i = ng;                  // first group with end > p
+        while (lo_i < hi_i) {
+            int mid = (lo_i + hi_i) >> 1;
+            if (gend[mid] > p) hi_i = mid; else lo_i = mid + 1;
+        }
+        int gi = lo_i;
+        if (gi >= ng) continue;
+        int32_t x = order[p];
+        if (fr_lt(hi[gi], Dn, un[x], ud[x])) { un[x] = hi[gi]; ud[x] = Dn; }
+        if (fr_lt(ln[x], ld[x], lo[gi], Dn)) { ln[x] = lo[gi]; ld[x] = Dn; }
+    }
+}
+
+// group id of every position (accepted groups 0..ng-1, remainder ng) and kept flag
+__global__ void group_keys_kernel(const int32_t* order, const int64_t* gend, int32_t ng, int32_t n, const uint8_t* status,
+                                  int32_t* gid, int32_t* keep, int32_t* gcount) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        int lo_i = 0, hi_i = ng;
+        while (lo_i < hi_i) {
+            int mid = (lo_i + hi_i) >> 1;
+            if (gend[mid] > p) hi_i = mid; else lo_i = mid + 1;
+        }
+        int32_t k = status[order[p]] == 0;
+        gid[p] = lo_i;
+        keep[p] = k;
+        if (k) atomicAdd(gcount + lo_i, 1);
+    }
+}
+
+__global__ void group_compact_kernel(const int32_t* order, const int32_t* keep, const int64_t* kpos, int32_t n,
+                                     int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        if (keep[p]) out[kpos[p]] = order[p];
+}
+
+// sub-round bounds: ub_sub = min(core_sub, ub_G of the same vertex)
+__global__ void sub_bounds_kernel(const int32_t* sub_to_orig, const int32_t* comp, int32_t nsub, const int64_t* unG,
+                                  const int64_t* udG, int64_t* un, int64_t* ud) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nsub; x += stride) {
+        int32_t gx = comp[sub_to_orig[x]];
+        if (fr_lt(unG[gx], udG[gx], un[x], ud[x])) { un[x] = unG[gx]; ud[x] = udG[gx]; }
+    }
+}
+
+// lift lower bounds of a sub-round to G
+__global__ void lift_lb_kernel(const int32_t* sub_to_orig, const int32_t* comp, int32_t nsub, const int64_t* ln,
+                               const int64_t* ld, int64_t* lnG, int64_t* ldG) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nsub; x += stride) {
+        int32_t gx = comp[sub_to_orig[x]];
+        if (fr_lt(lnG[gx], ldG[gx], ln[x], ld[x])) { lnG[gx] = ln[x]; ldG[gx] = ld[x]; }
+    }
+}
+
+// members given in sub internal ids -> G internal ids
+__global__ void to_parent_kernel(const int32_t* in, int64_t k, const int32_t* sub_to_orig, const int32_t* comp,
+                                 int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = comp[sub_to_orig[in[i]]];
+}
+
+// 1 if some vertex of the list has ub >= num / den
+__global__ void any_ub_ge_kernel(const int32_t* list, int32_t k, const int64_t* un, const int64_t* ud, int64_t num,
+                                 int64_t den, int32_t* flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        if (!fr_lt(un[x], ud[x], num, den)) *flag = 1;
+    }
+}
+
+__global__ void sort_keys_kernel(const int32_t* in, int64_t k, uint64_t* key) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) key[i] = (uint64_t)in[i];
+}
+
+__global__ void unsort_keys_kernel(const uint64_t* key, int64_t k, int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (int32_t)key[i];
+}
+
+// ---- exact settle helpers (compact numbers of a small vertex set)
+
+__global__ void reduce_patterns_count_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* inB,
+                                             int32_t* len) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        int32_t c = 0;
+        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a) c += !inB[pidx[a]];
+        len[j] = c;
+    }
+}
+
+__global__ void reduce_patterns_fill_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* inB,
+                                            const int32_t* freeidx, const int64_t* nptr, int32_t* nidx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        int64_t o = nptr[j];
+        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a)
+            if (!inB[pidx[a]]) nidx[o++] = freeidx[pidx[a]];
+    }
+}
+
+__global__ void pattern_inside_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* in,
+                                      int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t c = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        bool all = pptr[j + 1] > pptr[j];
+        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a) all &= in[pidx[a]] != 0;
+        c += all;
+    }
+    if (c) atomicAdd(cnt, c);
+}
+
+__global__ void u8_count_kernel(const uint8_t* f, int64_t k, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) c += f[i] != 0;
+    if (c) atomicAdd(cnt, c);
+}
+
+}  // namespace
+
+struct Timers {
+    double fw = 0, sg = 0, prune = 0, verify = 0, refine = 0, total = 0;
+};
+
+struct Driver {
+    lds_graph* G;
+    bool tri;
+    int32_t k;
+    int32_t N;
+    lds_precision prec;
+    bool include_zero;
+    Bounds bG;
+    Scratch sc;
+    VerifyStats vst;
+    lds_topk_stats_t stats{};
+    Timers tm;
+    struct Found {
+        int64_t num, den;
+        std::vector<int32_t> members;          // G internal ids, ascending
+    };
+    std::vector<Found> found;
+
+    Driver(lds_graph* g, bool t, int32_t kk, int32_t n, lds_precision p, bool iz)
+        : G(g), tri(t), k(kk), N(n), prec(p), include_zero(iz), sc(g) {}
+
+    cudaStream_t st() const { return G->stream; }
+
+    void init_bounds(lds_graph* g, Bounds& b) {
+        cudaStream_t s = g->stream;
+        const int32_t n = g->n;
+        b.un.alloc(std::max(n, 1), s);
+        b.ud.alloc(std::max(n, 1), s);
+        b.ln.alloc(std::max(n, 1), s);
+        b.ld.alloc(std::max(n, 1), s);
+        DevBuf<int64_t> core(std::max(g->nact, 1), s);
+        core_numbers(g, tri, core.get(), nullptr);
+        if (n) LDS_LAUNCH(init_bounds_kernel, grid_for(n, DB), DB, 0, s, core.get(), g->nact, n, tri ? 3 : 2, b.un.get(),
+                          b.ud.get(), b.ln.get(), b.ld.get());
+    }
+
+    // FW + ExtractSG + Pruning on handle h with bounds b (tightened in place).
+    // Returns the kept members of every group (h internal ids) and group offsets.
+    void round(lds_graph* h, Bounds& b, int32_t iters, DevBuf<int32_t>& members, std::vector<int64_t>& offs) {
+        cudaStream_t s = h->stream;
+        auto t0 = std::chrono::steady_clock::now();
+        fw_run(h, tri ? LDS_TRIANGLE : LDS_EDGE, iters, prec, false);
+        ++stats.fw_rounds;
+        stats.fw_edge_updates += (tri ? h->ntri : h->m) * (int64_t)iters;
+        auto t1 = std::chrono::steady_clock::now();
+        SgState sg;
+        extract_sg(h, sg);
+        const int32_t n = h->n;
+        const int32_t ng = (int32_t)sg.group_end.size();
+        DevBuf<int64_t> gend(std::max(ng, 1), s), lo(std::max(ng, 1), s), hi(std::max(ng, 1), s);
+        if (ng) {
+            std::vector<int64_t> l(sg.lo.begin(), sg.lo.end()), hh(sg.hi.begin(), sg.hi.end());
+            copy_in(gend.get(), sg.group_end.data(), LDS_MEM_HOST, ng * sizeof(int64_t), s);
+            copy_in(lo.get(), l.data(), LDS_MEM_HOST, ng * sizeof(int64_t), s);
+            copy_in(hi.get(), hh.data(), LDS_MEM_HOST, ng * sizeof(int64_t), s);
+            int64_t npos = sg.group_end.back();
+            LDS_LAUNCH(apply_groups_kernel, grid_for(npos, DB), DB, 0, s, sg.order.get(), gend.get(), lo.get(), hi.get(),
+                       ng, sg.D, npos, b.un.get(), b.ud.get(), b.ln.get(), b.ld.get());
+        }
+        auto t2 = std::chrono::steady_clock::now();
+        DevBuf<uint8_t> status(std::max(n, 1), s);
+        prune(h, tri, b.un.get(), b.ud.get(), b.ln.get(), b.ld.get(), status.get());
+        // kept members per group (the remainder is one more group)
+        DevBuf<int32_t> gid(std::max(n, 1), s), keep(std::max(n, 1), s), gcount(ng + 1, s);
+        LDS_CUDA(cudaMemsetAsync(gcount.get(), 0, (ng + 1) * sizeof(int32_t), s));
+        if (n) LDS_LAUNCH(group_keys_kernel, grid_for(n, DB), DB, 0, s, sg.order.get(), gend.get(), ng, n, status.get(),
+                          gid.get(), keep.get(), gcount.get());
+        DevBuf<int64_t> kpos(std::max(n, 1), s);
+        int64_t nk = exclusive_scan_i32_to_i64(keep.get(), kpos.get(), n, s);
+        members.alloc(std::max<int64_t>(nk, 1), s);
+        if (n) LDS_LAUNCH(group_compact_kernel, grid_for(n, DB), DB, 0, s, sg.order.get(), keep.get(), kpos.get(), n,
+                          members.get());
+        std::vector<int32_t> hc(ng + 1);
+        LDS_CUDA(cudaMemcpyAsync(hc.data(), gcount.get(), (ng + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        offs.assign(1, 0);
+        for (int32_t c : hc)
+            if (c) offs.push_back(offs.back() + c);
+        auto t3 = std::chrono::steady_clock::now();
+        tm.fw += std::chrono::duration<double, std::milli>(t1 - t0).count();
+        tm.sg += std::chrono::duration<double, std::milli>(t2 - t1).count();
+        tm.prune += std::chrono::duration<double, std::milli>(t3 - t2).count();
+    }
+
+    bool kth(int64_t& num, int64_t& den) {
+        if ((int32_t)found.size() < k) return false;
+        std::vector<std::pair<int64_t, int64_t>> ds;
+        for (auto& f : found) ds.push_back({f.num, f.den});
+        std::sort(ds.begin(), ds.end(), [](auto& a, auto& b) { return (i128)a.first * b.second > (i128)b.first * a.second; });
+        num = ds[k - 1].first;
+        den = ds[k - 1].second;
+        return true;
+    }
+
+    void certify(const int32_t* comp, int32_t csize, int64_t npat) {
+        if (npat == 0 && !include_zero) return;
+        bool ok = is_lds(G, tri, comp, csize, npat, bG, sc, &vst);
+        if (ok) {
+            Found f;
+            int64_t g = std::gcd(npat, (int64_t)csize);
+            f.num = npat / g;
+            f.den = csize / g;
+            f.members.resize(csize);
+            LDS_CUDA(cudaMemcpyAsync(f.members.data(), comp, csize * sizeof(int32_t), cudaMemcpyDeviceToHost, st()));
+            LDS_CUDA(cudaStreamSynchronize(st()));
+            found.push_back(std::move(f));
+            ++stats.certified;
+        } else {
+            ++stats.failed;
+        }
+    }
+
+    // Compact numbers of G[comp] by the density-friendly decomposition, then the
+    // LDSs of G[comp] (level-set components with no denser neighbour inside
+    // comp), each certified on G.
+    void exact_settle(const int32_t* comp, int32_t csize);
+
+    void run();
+};
+
+void Driver::exact_settle(const int32_t* comp, int32_t csize) {
+    ++stats.exact_settled;
+    cudaStream_t s = st();
+    lds_graph* h = subgraph(G, comp, csize, sc);
+    struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+    if (tri) ensure_triangles(h);
+    const int32_t n = h->n;
+    // patterns of G[comp] in h's original ids (= positions in comp)
+    Scratch shc(h);
+    DevBuf<int32_t> all(std::max(n, 1), s);
+    {
+        std::vector<int32_t> ids(n);
+        std::iota(ids.begin(), ids.end(), 0);
+        DevBuf<int32_t> orig(std::max(n, 1), s);
+        copy_in(orig.get(), ids.data(), LDS_MEM_HOST, n * sizeof(int32_t), s);
+        map_ids(orig.get(), h->to_int.get(), n, all.get(), s);   // internal ids of h, in original order
+        LDS_CUDA(cudaStreamSynchronize(s));
+    }
+    // patterns over h's internal ids with local index = original id
+    DevBuf<int64_t> pptr;
+    DevBuf<int32_t> pidx;
+    int64_t np = build_all_patterns(h, tri, all.get(), n, shc, pptr, pidx);
+    // decomposition: phi per local vertex as (num, den)
+    std::vector<int64_t> phin(n, -1), phid(n, 1);
+    std::vector<uint8_t> inB(n, 0);
+    DevBuf<uint8_t> dB(std::max(n, 1), s), side(std::max(n, 1), s);
+    DevBuf<int32_t> freeidx(std::max(n, 1), s), cnt(1, s);
+    int32_t assigned = 0;
+    while (assigned < n) {
+        // free vertices and their local indices
+        std::vector<int32_t> fidx(n, -1), freev;
+        for (int32_t x = 0; x < n; ++x)
+            if (!inB[x]) { fidx[x] = (int32_t)freev.size(); freev.push_back(x); }
+        const int32_t nf = (int32_t)freev.size();
+        copy_in(dB.get(), inB.data(), LDS_MEM_HOST, n, s);
+        copy_in(freeidx.get(), fidx.data(), LDS_MEM_HOST, n * sizeof(int32_t), s);
+        DevBuf<int32_t> len(std::max<int64_t>(np, 1) + 1, s);
+        LDS_CUDA(cudaMemsetAsync(len.get(), 0, (std::max<int64_t>(np, 1) + 1) * sizeof(int32_t), s));
+        if (np) LDS_LAUNCH(reduce_patterns_count_kernel, grid_for(np, DB), DB, 0, s, pptr.get(), pidx.get(), np, dB.get(),
+                           len.get());
+        DevBuf<int64_t> nptr(np + 1, s);
+        int64_t nidx = exclusive_scan_i32_to_i64(len.get(), nptr.get(), np + 1, s);
+        DevBuf<int32_t> ridx(std::max<int64_t>(nidx, 1), s);
+        if (np) LDS_LAUNCH(reduce_patterns_fill_kernel, grid_for(np, DB), DB, 0, s, pptr.get(), pidx.get(), np, dB.get(),
+                           freeidx.get(), nptr.get(), ridx.get());
+        // drop patterns that lie inside B (length 0): they cannot be cut and carry no free vertex;
+        // keep them out by counting only the non-empty ones
+        std::vector<int64_t> hptr(np + 1);
+        LDS_CUDA(cudaMemcpyAsync(hptr.data(), nptr.get(), (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> cptr(1, 0);
+        for (int64_t j = 0; j < np; ++j)
+            if (hptr[j + 1] > hptr[j]) cptr.push_back(hptr[j + 1]);
+        const int64_t nr = (int64_t)cptr.size() - 1;
+        DevBuf<int64_t> dptr(nr + 1, s);
+        copy_in(dptr.get(), cptr.data(), LDS_MEM_HOST, (nr + 1) * sizeof(int64_t), s);
+        // Dinkelbach from the ratio of taking every free vertex
+        int64_t p = nr, q = nf;
+        {
+            int64_t g = std::gcd(p, q);
+            if (g) { p /= g; q /= g; }
+        }
+        if (p == 0) q = 1;
+        std::vector<uint8_t> X(nf, 1);
+        for (int it = 0;; ++it) {
+            int64_t f = pattern_max_flow(dptr.get(), ridx.get(), (int32_t)nr, nf, p, q, side.get(), s);
+            ++vst.flows;
+            int64_t value = q * nr - f;
+            std::vector<uint8_t> hs(nf);
+            LDS_CUDA(cudaMemcpyAsync(hs.data(), side.get(), nf, cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            if (value <= 0) {
+                X = hs;
+                break;
+            }
+            // ratio of the maximiser X
+            LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
+            LDS_LAUNCH(pattern_inside_kernel, grid_for(std::max<int64_t>(nr, 1), DB), DB, 0, s, dptr.get(), ridx.get(), nr,
+                       side.get(), cnt.get());
+            int32_t inside = 0;
+            LDS_CUDA(cudaMemcpyAsync(&inside, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            int64_t xs = 0;
+            for (uint8_t b : hs) xs += b;
+            int64_t g = std::gcd((int64_t)inside, xs);
+            p = inside / g;
+            q = xs / g;
+            LDS_REQUIRE(it < 4 * nf + 8, LDS_ETIMEOUT, "exact settle: Dinkelbach did not converge");
+        }
+        int64_t xs = 0;
+        for (uint8_t b : X) xs += b;
+        if (xs == 0) std::fill(X.begin(), X.end(), 1);      // ratio 0: everything left
+        for (int32_t i = 0; i < nf; ++i)
+            if (X[i]) {
+                int32_t x = freev[i];
+                phin[x] = p;
+                phid[x] = q;
+                inB[x] = 1;
+                ++assigned;
+            }
+    }
+    // LDSs of G[comp]: components of level sets with no neighbour of higher phi inside comp
+    std::vector<std::pair<int64_t, int64_t>> levels;
+    for (int32_t x = 0; x < n; ++x) levels.push_back({phin[x], phid[x]});
+    std::sort(levels.begin(), levels.end());
+    levels.erase(std::unique(levels.begin(), levels.end()), levels.end());
+    std::vector<int32_t> hcomp(csize);
+    LDS_CUDA(cudaMemcpyAsync(hcomp.data(), comp, csize * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    for (auto& lv : levels) {
+        if (lv.first == 0 && !include_zero) continue;
+        std::vector<int32_t> memb;
+        for (int32_t x = 0; x < n; ++x)
+            if (phin[x] == lv.first && phid[x] == lv.second) memb.push_back(hcomp[x]);
+        DevBuf<int32_t> dm(memb.size(), s);
+        copy_in(dm.get(), memb.data(), LDS_MEM_HOST, memb.size() * sizeof(int32_t), s);
+        DevBuf<int32_t> cm;
+        std::vector<int32_t> cs;
+        components(G, dm.get(), (int32_t)memb.size(), sc, cm, cs);
+        for (size_t c = 0; c + 1 < cs.size(); ++c) {
+            int64_t npat = 0;
+            const int32_t* cp = cm.get() + cs[c];
+            int32_t csz = cs[c + 1] - cs[c];
+            if (is_densest(G, tri, cp, csz, sc, &npat)) certify(cp, csz, npat);
+        }
+    }
+}
+
+void Driver::run() {
+    auto T0 = std::chrono::steady_clock::now();
+    cudaStream_t s = st();
+    if (tri) ensure_triangles(G);
+    init_bounds(G, bG);
+    DevBuf<int32_t> members;
+    std::vector<int64_t> offs;
+    round(G, bG, N, members, offs);
+    struct Item {
+        std::shared_ptr<DevBuf<int32_t>> buf;
+        int64_t off, size;
+    };
+    std::vector<Item> stack;
+    auto mshared = std::make_shared<DevBuf<int32_t>>(std::move(members));
+    for (size_t gidx = offs.size() - 1; gidx-- > 0;)
+        stack.push_back({mshared, offs[gidx], offs[gidx + 1] - offs[gidx]});
+    while (!stack.empty()) {
+        Item it = stack.back();
+        stack.pop_back();
+        const int32_t* S = it.buf->get() + it.off;
+        const int32_t ssz = (int32_t)it.size;
+        int64_t rkn, rkd;
+        if (kth(rkn, rkd)) {
+            DevBuf<int32_t> flag(1, s);
+            LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
+            LDS_LAUNCH(any_ub_ge_kernel, grid_for(ssz, DB), DB, 0, s, S, ssz, bG.un.get(), bG.ud.get(), rkn, rkd, flag.get());
+            int32_t hf = 0;
+            LDS_CUDA(cudaMemcpyAsync(&hf, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            if (!hf) {
+                ++stats.skipped_by_bound;
+                continue;
+            }
+        }
+        // components of G[S], members ascending
+        DevBuf<int32_t> sorted(std::max(ssz, 1), s);
+        {
+            DevBuf<uint64_t> key(std::max(ssz, 1), s);
+            LDS_LAUNCH(sort_keys_kernel, grid_for(ssz, DB), DB, 0, s, S, ssz, key.get());
+            radix_sort_u64(key.get(), nullptr, ssz, bit_length_u64((uint64_t)std::max(G->n, 1)), s);
+            LDS_LAUNCH(unsort_keys_kernel, grid_for(ssz, DB), DB, 0, s, key.get(), ssz, sorted.get());
+        }
+        DevBuf<int32_t> cm;
+        std::vector<int32_t> cs;
+        auto tv0 = std::chrono::steady_clock::now();
+        components(G, sorted.get(), ssz, sc, cm, cs);
+        auto cmh = std::make_shared<DevBuf<int32_t>>(std::move(cm));
+        for (size_t c = 0; c + 1 < cs.size(); ++c) {
+            const int32_t* comp = cmh->get() + cs[c];
+            const int32_t csize = cs[c + 1] - cs[c];
+            int64_t npat = 0;
+            auto tv1 = std::chrono::steady_clock::now();
+            bool dens = is_densest(G, tri, comp, csize, sc, &npat);
+            if (dens) {
+                certify(comp, csize, npat);
+                tm.verify += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv1).count();
+                continue;
+            }
+            tm.verify += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv1).count();
+            // refine on G[comp]
+            int32_t n_try = N;
+            while (true) {
+                ++stats.refined;
+                lds_graph* h = subgraph(G, comp, csize, sc);
+                struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+                Bounds bs;
+                init_bounds(h, bs);
+                if (h->n)
+                    LDS_LAUNCH(sub_bounds_kernel, grid_for(h->n, DB), DB, 0, s, h->to_orig.get(), comp, h->n,
+                               bG.un.get(), bG.ud.get(), bs.un.get(), bs.ud.get());
+                DevBuf<int32_t> sm;
+                std::vector<int64_t> so;
+                round(h, bs, n_try, sm, so);
+                if (h->n)
+                    LDS_LAUNCH(lift_lb_kernel, grid_for(h->n, DB), DB, 0, s, h->to_orig.get(), comp, h->n, bs.ln.get(),
+                               bs.ld.get(), bG.ln.get(), bG.ld.get());
+                const int64_t nsub = so.back();
+                bool progress = !(so.size() == 2 && nsub == csize);
+                if (progress) {
+                    auto mp = std::make_shared<DevBuf<int32_t>>(std::max<int64_t>(nsub, 1), s);
+                    if (nsub)
+                        LDS_LAUNCH(to_parent_kernel, grid_for(nsub, DB), DB, 0, s, sm.get(), nsub, h->to_orig.get(), comp,
+                                   mp->get());
+                    LDS_CUDA(cudaStreamSynchronize(s));
+                    for (size_t gidx = so.size() - 1; gidx-- > 0;)
+                        stack.push_back({mp, so[gidx], so[gidx + 1] - so[gidx]});
+                    break;
+                }
+                if (n_try >= 8 * N) {
+                    exact_settle(comp, csize);
+                    break;
+                }
+                n_try *= 2;
+            }
+        }
+        tm.refine += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv0).count();
+    }
+    stats.flows = vst.flows;
+    stats.denser_neighbour = vst.denser_neighbour;
+    tm.total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - T0).count();
+    stats.ms_total = tm.total;
+    stats.ms_fw = tm.fw;
+    stats.ms_extract = tm.sg;
+    stats.ms_prune = tm.prune;
+    stats.ms_verify = tm.verify;
+}
+
+}  // namespace lds
+
+using namespace lds;
+
+namespace {
+thread_local lds_topk_stats_t t_last_stats{};
+}
+
+extern "C" {
+
+lds_status lds_topk(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, lds_result** out) {
+    return guard([&] {
+        LDS_REQUIRE(g && out, LDS_EINVAL, "lds_topk: NULL argument");
+        LDS_REQUIRE(k >= 1, LDS_EINVAL, "lds_topk: k = %d < 1", k);
+        LDS_REQUIRE(d == LDS_EDGE || d == LDS_TRIANGLE, LDS_EINVAL, "lds_topk: bad density");
+        LDS_REQUIRE(iters >= 1 && iters <= (d == LDS_EDGE ? 7000 : 3500), LDS_EINVAL,
+                    "lds_topk: iters = %d out of range (refinement may run 8x iters)", iters);
+        LDS_REQUIRE(p == LDS_EXACT || p == LDS_FP32 || p == LDS_FP64, LDS_EINVAL, "lds_topk: bad precision");
+        *out = nullptr;
+        Driver drv(g, d == LDS_TRIANGLE, k, iters, p, false);
+        drv.run();
+        // order: density descending, ties by smallest member id (original ids)
+        struct R {
+            int64_t num, den;
+            std::vector<int32_t> orig;
+        };
+        std::vector<R> rs;
+        std::vector<int32_t> to_orig(g->n);
+        if (g->n) {
+            LDS_CUDA(cudaMemcpyAsync(to_orig.data(), g->to_orig.get(), g->n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                     g->stream));
+            LDS_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        for (auto& f : drv.found) {
+            R r{f.num, f.den, {}};
+            for (int32_t x : f.members) r.orig.push_back(to_orig[x]);
+            std::sort(r.orig.begin(), r.orig.end());
+            rs.push_back(std::move(r));
+        }
+        std::sort(rs.begin(), rs.end(), [](const R& a, const R& b) {
+            i128 l = (i128)a.num * b.den, r = (i128)b.num * a.den;
+            if (l != r) return l > r;
+            return a.orig[0] < b.orig[0];
+        });
+        if ((int32_t)rs.size() > k) rs.resize(k);
+        lds_result* res = (lds_result*)calloc(1, sizeof(lds_result));
+        LDS_REQUIRE(res, LDS_ENOMEM, "lds_topk: host allocation failed");
+        int64_t total = 0;
+        for (auto& r : rs) total += (int64_t)r.orig.size();
+        res->count = (int32_t)rs.size();
+        res->dens_num = (int64_t*)malloc(sizeof(int64_t) * std::max<size_t>(rs.size(), 1));
+        res->dens_den = (int64_t*)malloc(sizeof(int64_t) * std::max<size_t>(rs.size(), 1));
+        res->offsets = (int64_t*)malloc(sizeof(int64_t) * (rs.size() + 1));
+        res->vertices = (int32_t*)malloc(sizeof(int32_t) * std::max<int64_t>(total, 1));
+        if (!res->dens_num || !res->dens_den || !res->offsets || !res->vertices) {
+            lds_result_free(res);
+            LDS_REQUIRE(false, LDS_ENOMEM, "lds_topk: host allocation failed");
+        }
+        res->offsets[0] = 0;
+        for (size_t i = 0; i < rs.size(); ++i) {
+            res->dens_num[i] = rs[i].num;
+            res->dens_den[i] = rs[i].den;
+            std::memcpy(res->vertices + res->offsets[i], rs[i].orig.data(), rs[i].orig.size() * sizeof(int32_t));
+            res->offsets[i + 1] = res->offsets[i] + (int64_t)rs[i].orig.size();
+        }
+        t_last_stats = drv.stats;
+        *out = res;
+    });
+}
+
+void lds_result_free(lds_result* r) {
+    if (!r) return;
+    free(r->dens_num);
+    free(r->dens_den);
+    free(r->offsets);
+    free(r->vertices);
+    free(r);
+}
+
+lds_status lds_topk_last_stats(lds_topk_stats_t* st) {
+    return guard([&] {
+        LDS_REQUIRE(st, LDS_EINVAL, "lds_topk_last_stats: NULL argument");
+        *st = t_last_stats;
+    });
+}
+
+}  // extern "C"

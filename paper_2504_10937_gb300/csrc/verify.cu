@@ -1,0 +1,634 @@
+// Candidate verification on the GPU: IsDensest (Sec. 5.4), IsLDS (Alg. 4),
+// IsLTDS (Alg. 7) with ExtMaximal (Alg. 8), plus the helpers the driver needs
+// (connected components of G[S], subgraph handles, exact compact numbers of a
+// small vertex set).
+//
+// IsDensest(S): G[S] is its own densest subgraph iff the pattern network over
+// S (patterns E(S) or T(S), rho = density) saturates every source arc, i.e.
+// the maximum flow is q |P| for rho = p / q.
+//
+// IsLDS(S): rho = |E(S)| / |S|.  A neighbour w outside S with lb(w) > rho
+// rejects S at once (phi(w) > rho, Lemma 3).  Otherwise U is grown from S over
+// neighbours w with lb(w) <= rho <= ub(w) (a level-synchronous search; the set
+// does not depend on the visiting order), every edge from a U vertex v to a
+// vertex w outside U with lb(w) > rho becomes a loop pattern {v}, and the
+// maximum flow over U with patterns E(U) plus the loops yields A, the largest
+// source side (= {u in U : phi(u) >= rho}, Lemma 9).  S is an LDS iff S is a
+// connected component of G[A].  When U = S no flow is needed.
+//
+// IsLTDS(S): the same with tr-density; the patterns are, for every triangle
+// with a vertex in U and all three upper bounds >= rho, its vertices with
+// lb <= rho (Alg. 7).  Those vertices are reached by the edge search as well,
+// so U is the same edge-grown set.
+#include <algorithm>
+#include <numeric>
+
+#include "flow.cuh"
+#include "prims.cuh"
+#include "verify.cuh"
+
+namespace lds {
+
+namespace {
+
+typedef __int128 i128;
+constexpr int VB = 256;
+
+// num / den compared with p / q
+__device__ __forceinline__ bool gt_rho(int64_t num, int64_t den, int64_t p, int64_t q) {
+    return (i128)num * q > (i128)p * den;
+}
+__device__ __forceinline__ bool lt_rho(int64_t num, int64_t den, int64_t p, int64_t q) {
+    return (i128)num * q < (i128)p * den;
+}
+
+__global__ void mark_kernel(const int32_t* list, int32_t k, uint8_t* flag, int32_t* local) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        flag[list[i]] = 1;
+        if (local) local[list[i]] = (int32_t)i;
+    }
+}
+
+__global__ void unmark_kernel(const int32_t* list, int32_t k, uint8_t* flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) flag[list[i]] = 0;
+}
+
+// per member x: number of edge patterns it owns (neighbours y in the set with y > x)
+__global__ void edge_pat_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                                      const int32_t* col, const uint8_t* in, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i], c = 0;
+        if (x < nact)
+            for (int64_t q = rowptr[x]; q < rowptr[x + 1]; ++q) {
+                int32_t y = col[q];
+                c += (y > x && in[y]);
+            }
+        cnt[i] = c;
+    }
+}
+
+__global__ void edge_pat_fill_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                                     const int32_t* col, const uint8_t* in, const int32_t* local, const int64_t* off,
+                                     int32_t* pidx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        int64_t o = off[i];
+        if (x < nact)
+            for (int64_t q = rowptr[x]; q < rowptr[x + 1]; ++q) {
+                int32_t y = col[q];
+                if (y > x && in[y]) {
+                    pidx[2 * o] = (int32_t)i;
+                    pidx[2 * o + 1] = local[y];
+                    ++o;
+                }
+            }
+    }
+}
+
+// loops: members v with neighbours w outside the set and lb(w) > rho
+__global__ void loop_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr, const int32_t* col,
+                                  const uint8_t* in, const int64_t* ln, const int64_t* ld, int64_t p, int64_t q,
+                                  int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i], c = 0;
+        if (x < nact)
+            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+                int32_t w = col[r];
+                c += (!in[w] && gt_rho(ln[w], ld[w], p, q));
+            }
+        cnt[i] = c;
+    }
+}
+
+__global__ void uniform_pat_ptr_kernel(int64_t np, int64_t width, int64_t* pptr) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= np; j += stride) pptr[j] = j * width;
+}
+
+__global__ void loop_fill_kernel(const int32_t* cnt, const int64_t* off, int32_t k, int32_t* pidx, int64_t base) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
+        for (int32_t c = 0; c < cnt[i]; ++c) pidx[base + off[i] + c] = (int32_t)i;
+}
+
+// triangles owned by their smallest member that is in the set (only those
+// with all vertices in the set when `all_in`), else for IsLTDS: triangles with a
+// member in the set and all ub >= rho, reduced to vertices with lb <= rho
+template <bool FILL>
+__global__ void tri_pat_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* vt_ptr,
+                               const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                               const uint8_t* in, const int32_t* local, bool all_in, const int64_t* un,
+                               const int64_t* ud, const int64_t* ln, const int64_t* ld, int64_t p, int64_t q,
+                               int32_t* cnt, int32_t* len, const int64_t* off, int64_t* pptr, int32_t* pidx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        int32_t c = 0, l = 0;
+        int64_t o = FILL ? off[i] : 0;
+        if (x < nact)
+            for (int64_t r = vt_ptr[x]; r < vt_ptr[x + 1]; ++r) {
+                int32_t t = vt_idx[r];
+                int32_t v[3] = {ta[t], tb[t], tc[t]};
+                // owner: smallest member in the set
+                int32_t owner = -1;
+                for (int j = 0; j < 3; ++j)
+                    if (in[v[j]] && (owner < 0 || v[j] < owner)) owner = v[j];
+                if (owner != x) continue;
+                if (all_in) {
+                    if (!(in[v[0]] && in[v[1]] && in[v[2]])) continue;
+                    if (FILL)
+                        for (int j = 0; j < 3; ++j) pidx[3 * o + j] = local[v[j]];
+                    ++c;
+                    l += 3;
+                    ++o;
+                } else {
+                    bool valid = true;
+                    for (int j = 0; j < 3; ++j)
+                        if (lt_rho(un[v[j]], ud[v[j]], p, q)) valid = false;
+                    if (!valid) continue;
+                    // members with lb <= rho (all of them lie in U; the test on `in`
+                    // only guards the local index)
+                    int32_t mm = 0;
+                    for (int j = 0; j < 3; ++j)
+                        if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) ++mm;
+                    if (mm == 0) continue;
+                    if (FILL) {
+                        int64_t at = pptr[o];
+                        for (int j = 0; j < 3; ++j)
+                            if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) pidx[at++] = local[v[j]];
+                    }
+                    ++c;
+                    l += mm;
+                    ++o;
+                }
+            }
+        if (!FILL) {
+            cnt[i] = c;
+            len[i] = l;
+        }
+    }
+}
+
+// length of every reduced triangle pattern, in the order tri_pat_kernel emits them
+__global__ void tri_len_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* vt_ptr, const int32_t* vt_idx,
+                               const int32_t* ta, const int32_t* tb, const int32_t* tc, const uint8_t* in,
+                               const int64_t* un, const int64_t* ud, const int64_t* ln, const int64_t* ld, int64_t p,
+                               int64_t q, const int64_t* off, int32_t* plen) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        int64_t o = off[i];
+        if (x >= nact) continue;
+        for (int64_t r = vt_ptr[x]; r < vt_ptr[x + 1]; ++r) {
+            int32_t t = vt_idx[r];
+            int32_t v[3] = {ta[t], tb[t], tc[t]};
+            int32_t owner = -1;
+            for (int j = 0; j < 3; ++j)
+                if (in[v[j]] && (owner < 0 || v[j] < owner)) owner = v[j];
+            if (owner != x) continue;
+            bool valid = true;
+            for (int j = 0; j < 3; ++j)
+                if (lt_rho(un[v[j]], ud[v[j]], p, q)) valid = false;
+            if (!valid) continue;
+            int32_t mm = 0;
+            for (int j = 0; j < 3; ++j)
+                if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) ++mm;
+            if (mm == 0) continue;
+            plen[o++] = mm;
+        }
+    }
+}
+
+__global__ void add_offset_i64_kernel(int64_t* p, int64_t k, int64_t off) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) p[i] += off;
+}
+
+__global__ void widen_i32_u64_kernel(const int32_t* in, int64_t k, uint64_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (uint64_t)in[i];
+}
+
+__global__ void narrow_u64_i32_kernel(const uint64_t* in, int64_t k, int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (int32_t)in[i];
+}
+
+// one level of the search that grows U over neighbours with lb <= rho <= ub
+__global__ void grow_level_kernel(const int32_t* frontier, int32_t fsize, int32_t nact, const int64_t* rowptr,
+                                  const int32_t* col, uint8_t* inU, const int64_t* un, const int64_t* ud,
+                                  const int64_t* ln, const int64_t* ld, int64_t p, int64_t q, int32_t* next,
+                                  int32_t* nsize) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fsize; i += stride) {
+        int32_t x = frontier[i];
+        if (x >= nact) continue;
+        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+            int32_t w = col[r];
+            if (inU[w]) continue;
+            if (gt_rho(ln[w], ld[w], p, q)) continue;         // loop side, never joins U
+            if (lt_rho(un[w], ud[w], p, q)) continue;         // phi(w) < rho
+            unsigned int* word = (unsigned int*)(inU + (w & ~3));
+            unsigned int bit = 1u << (8 * (w & 3));
+            if (!(atomicOr(word, bit) & bit)) next[atomicAdd(nsize, 1)] = w;
+        }
+    }
+}
+
+// any neighbour outside S with lb > rho
+__global__ void denser_neighbour_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                                        const int32_t* col, const uint8_t* inS, const int64_t* ln, const int64_t* ld,
+                                        int64_t p, int64_t q, int32_t* flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        if (x >= nact) continue;
+        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+            int32_t w = col[r];
+            if (!inS[w] && gt_rho(ln[w], ld[w], p, q)) {
+                atomicOr(flag, 1);
+                return;
+            }
+        }
+    }
+}
+
+__global__ void collect_kernel(const uint8_t* flag, int32_t n, int32_t* out, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        if (flag[x]) out[atomicAdd(cnt, 1)] = (int32_t)x;
+}
+
+// S must lie in A and have no neighbour in A outside S
+__global__ void component_check_kernel(const int32_t* S, int32_t k, int32_t nact, const int64_t* rowptr,
+                                       const int32_t* col, const uint8_t* inS, const uint8_t* inA, int32_t* bad) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = S[i];
+        if (!inA[x]) { atomicOr(bad, 1); continue; }
+        if (x >= nact) continue;
+        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+            int32_t w = col[r];
+            if (inA[w] && !inS[w]) { atomicOr(bad, 1); break; }
+        }
+    }
+}
+
+__global__ void side_to_flag_kernel(const int32_t* U, int32_t nu, const uint8_t* side, uint8_t* inA) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += stride) inA[U[i]] = side[i];
+}
+
+// ---- components
+
+__global__ void cc_init_kernel(const int32_t* list, int32_t k, int32_t* label) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) label[list[i]] = list[i];
+}
+
+__global__ void cc_step_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr, const int32_t* col,
+                               const uint8_t* in, int32_t* label, int32_t* changed) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        if (x >= nact) continue;
+        int32_t lx = __ldcg(label + x);
+        int32_t best = lx;
+        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+            int32_t w = col[r];
+            if (in[w]) best = min(best, __ldcg(label + w));
+        }
+        if (best < lx) {
+            atomicMin(label + x, best);
+            *changed = 1;
+        }
+    }
+}
+
+__global__ void cc_keys_kernel(const int32_t* list, int32_t k, const int32_t* label, int bits, uint64_t* key) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
+        key[i] = ((uint64_t)label[list[i]] << bits) | (uint64_t)list[i];
+}
+
+__global__ void cc_unpack_kernel(const uint64_t* key, int32_t k, int bits, int32_t* members, int32_t* starts,
+                                 int32_t* nstart) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint64_t mask = (1ull << bits) - 1ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        members[i] = (int32_t)(key[i] & mask);
+        if (i == 0 || (key[i] >> bits) != (key[i - 1] >> bits)) starts[atomicAdd(nstart, 1)] = (int32_t)i;
+    }
+}
+
+// ---- subgraph
+
+__global__ void sub_edges_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                                       const int32_t* col, const uint8_t* in, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i], c = 0;
+        if (x < nact)
+            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) c += (col[r] > x && in[col[r]]);
+        cnt[i] = c;
+    }
+}
+
+__global__ void sub_edges_fill_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                                      const int32_t* col, const uint8_t* in, const int32_t* local, const int64_t* off,
+                                      int32_t* su, int32_t* sv) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
+        int32_t x = list[i];
+        int64_t o = off[i];
+        if (x < nact)
+            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+                int32_t y = col[r];
+                if (y > x && in[y]) {
+                    su[o] = (int32_t)i;
+                    sv[o] = local[y];
+                    ++o;
+                }
+            }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+
+Scratch::Scratch(lds_graph* g) : s(g->stream) {
+    in.alloc(std::max(g->n, 1) + 4, s);
+    in2.alloc(std::max(g->n, 1) + 4, s);
+    local.alloc(std::max(g->n, 1), s);
+    LDS_CUDA(cudaMemsetAsync(in.get(), 0, std::max(g->n, 1) + 4, s));
+    LDS_CUDA(cudaMemsetAsync(in2.get(), 0, std::max(g->n, 1) + 4, s));
+}
+
+static int64_t scan_counts(const int32_t* cnt, int64_t k, DevBuf<int64_t>& off, cudaStream_t s) {
+    off.alloc(k + 1, s);
+    DevBuf<int32_t> c1(k + 1, s);
+    LDS_CUDA(cudaMemsetAsync(c1.get(), 0, (k + 1) * sizeof(int32_t), s));
+    if (k) LDS_CUDA(cudaMemcpyAsync(c1.get(), cnt, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    return exclusive_scan_i32_to_i64(c1.get(), off.get(), k + 1, s);
+}
+
+static int64_t gcd64(int64_t a, int64_t b) {
+    while (b) {
+        int64_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Builds the pattern lists over `list` (k members, marked in sc.in with local
+// indices in sc.local).  Edge density: E(list) (+ loops when `loops` is set);
+// triangle density: T(list) when all_in, else Alg. 7's reduced patterns.
+static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch& sc, bool all_in,
+                              bool loops, const Bounds* b, int64_t p, int64_t q, DevBuf<int64_t>& pptr,
+                              DevBuf<int32_t>& pidx, int64_t* n_main) {
+    cudaStream_t s = g->stream;
+    const int32_t nact = g->nact;
+    DevBuf<int32_t> cnt(std::max(k, 1), s), len(std::max(k, 1), s);
+    DevBuf<int64_t> off;
+    if (!tri) {
+        if (k) LDS_LAUNCH(edge_pat_count_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+                          sc.in.get(), cnt.get());
+        int64_t ne = scan_counts(cnt.get(), k, off, s);
+        int64_t nl = 0;
+        DevBuf<int32_t> lcnt(std::max(k, 1), s);
+        DevBuf<int64_t> loff;
+        if (loops) {
+            if (k) LDS_LAUNCH(loop_count_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+                              sc.in.get(), b->ln.get(), b->ld.get(), p, q, lcnt.get());
+            nl = scan_counts(lcnt.get(), k, loff, s);
+        }
+        const int64_t np = ne + nl;
+        pptr.alloc(np + 1, s);
+        pidx.alloc(std::max<int64_t>(2 * ne + nl, 1), s);
+        // edge patterns first (width 2), then loops (width 1)
+        LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(ne + 1, VB), VB, 0, s, ne, 2, pptr.get());
+        if (nl) {
+            DevBuf<int64_t> tail(nl + 1, s);
+            LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(nl + 1, VB), VB, 0, s, nl, 1, tail.get());
+            LDS_LAUNCH(add_offset_i64_kernel, grid_for(nl + 1, VB), VB, 0, s, tail.get(), nl + 1, 2 * ne);
+            LDS_CUDA(cudaMemcpyAsync(pptr.get() + ne, tail.get(), (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        }
+        if (k && ne)
+            LDS_LAUNCH(edge_pat_fill_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+                       sc.in.get(), sc.local.get(), off.get(), pidx.get());
+        if (k && nl)
+            LDS_LAUNCH(loop_fill_kernel, grid_for(k, VB), VB, 0, s, lcnt.get(), loff.get(), k, pidx.get(), 2 * ne);
+        if (n_main) *n_main = ne;
+        return np;
+    }
+    ensure_vertex_triangles(g);
+    const Bounds* bb = b;
+    const int64_t* un = bb ? bb->un.get() : nullptr;
+    const int64_t* ud = bb ? bb->ud.get() : nullptr;
+    const int64_t* ln = bb ? bb->ln.get() : nullptr;
+    const int64_t* ld = bb ? bb->ld.get() : nullptr;
+    if (k)
+        LDS_LAUNCH(tri_pat_kernel<false>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
+                   g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
+                   cnt.get(), len.get(), (const int64_t*)nullptr, (int64_t*)nullptr, (int32_t*)nullptr);
+    int64_t np = scan_counts(cnt.get(), k, off, s);
+    DevBuf<int64_t> loffs;
+    int64_t nidx = scan_counts(len.get(), k, loffs, s);
+    pptr.alloc(np + 1, s);
+    pidx.alloc(std::max<int64_t>(nidx, 1), s);
+    if (all_in) {
+        LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(np + 1, VB), VB, 0, s, np, 3, pptr.get());
+    } else if (np) {
+        // pattern lengths are known only per owner; fill pattern starts with a pass that
+        // records each pattern's length, then scan
+        DevBuf<int32_t> plen(np + 1, s);
+        LDS_CUDA(cudaMemsetAsync(plen.get(), 0, (np + 1) * sizeof(int32_t), s));
+        LDS_LAUNCH(tri_len_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(),
+                   g->tb.get(), g->tc.get(), sc.in.get(), un, ud, ln, ld, p, q, off.get(), plen.get());
+        exclusive_scan_i32_to_i64(plen.get(), pptr.get(), np + 1, s);
+    }
+    if (k && np)
+        LDS_LAUNCH(tri_pat_kernel<true>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
+                   g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
+                   (int32_t*)nullptr, (int32_t*)nullptr, off.get(), all_in ? (int64_t*)nullptr : pptr.get(), pidx.get());
+    if (n_main) *n_main = np;
+    return np;
+}
+
+int64_t build_all_patterns(lds_graph* h, bool tri, const int32_t* list, int32_t k, Scratch& sc,
+                           DevBuf<int64_t>& pptr, DevBuf<int32_t>& pidx) {
+    cudaStream_t s = h->stream;
+    if (k) LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), sc.local.get());
+    int64_t np = build_patterns(h, tri, list, k, sc, true, false, nullptr, 0, 1, pptr, pidx, nullptr);
+    if (k) LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+    LDS_CUDA(cudaStreamSynchronize(s));
+    return np;
+}
+
+bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch& sc, int64_t* npat) {
+    cudaStream_t s = g->stream;
+    *npat = 0;
+    if (k == 0) return false;
+    LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), sc.local.get());
+    DevBuf<int64_t> pptr;
+    DevBuf<int32_t> pidx;
+    int64_t np = build_patterns(g, tri, list, k, sc, true, false, nullptr, 0, 1, pptr, pidx, nullptr);
+    *npat = np;
+    bool ok = true;
+    if (np > 0) {
+        int64_t gg = gcd64(np, k);
+        int64_t p = np / gg, q = k / gg;
+        int64_t f = pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, k, p, q, nullptr, s);
+        ok = f == q * np;
+    }
+    LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+    LDS_CUDA(cudaStreamSynchronize(s));
+    return ok;
+}
+
+bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat, const Bounds& b, Scratch& sc,
+            VerifyStats* st) {
+    cudaStream_t s = g->stream;
+    const int32_t n = g->n, nact = g->nact;
+    int64_t gg = gcd64(npat, k);
+    const int64_t p = npat / gg, q = k / gg;
+    LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), (int32_t*)nullptr);
+    DevBuf<int32_t> flag(1, s);
+    LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
+    LDS_LAUNCH(denser_neighbour_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+               sc.in.get(), b.ln.get(), b.ld.get(), p, q, flag.get());
+    int32_t hflag = 0;
+    LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    if (hflag) {
+        LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+        if (st) ++st->denser_neighbour;
+        return false;
+    }
+    // grow U from S (sc.in2 marks U)
+    DevBuf<int32_t> fa(std::max(n, 1), s), fb(std::max(n, 1), s), cnt(1, s);
+    LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get(), (int32_t*)nullptr);
+    LDS_CUDA(cudaMemcpyAsync(fa.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    int32_t fsize = k, usize = k;
+    int32_t* cur = fa.get();
+    int32_t* nxt = fb.get();
+    DevBuf<int32_t> U(std::max(n, 1), s);
+    LDS_CUDA(cudaMemcpyAsync(U.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    while (fsize > 0) {
+        LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
+        LDS_LAUNCH(grow_level_kernel, grid_for(fsize, VB), VB, 0, s, cur, fsize, nact, g->rowptr.get(), g->col.get(),
+                   sc.in2.get(), b.un.get(), b.ud.get(), b.ln.get(), b.ld.get(), p, q, nxt, cnt.get());
+        LDS_CUDA(cudaMemcpyAsync(&fsize, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        if (fsize) LDS_CUDA(cudaMemcpyAsync(U.get() + usize, nxt, fsize * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        usize += fsize;
+        std::swap(cur, nxt);
+    }
+    bool result;
+    if (usize == k) {
+        result = true;                   // U = S: no denser neighbour, no loop, nothing to add
+    } else {
+        // sort U ascending so local indices are deterministic
+        {
+            DevBuf<uint64_t> key(usize, s);
+            LDS_LAUNCH(widen_i32_u64_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, key.get());
+            radix_sort_u64(key.get(), nullptr, usize, bit_length_u64((uint64_t)std::max(n, 1)), s);
+            LDS_LAUNCH(narrow_u64_i32_kernel, grid_for(usize, VB), VB, 0, s, key.get(), usize, U.get());
+        }
+        // patterns over U: swap marks so that sc.in marks U with local indices
+        LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+        LDS_LAUNCH(mark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get(), sc.local.get());
+        DevBuf<int64_t> pptr;
+        DevBuf<int32_t> pidx;
+        int64_t np = build_patterns(g, tri, U.get(), usize, sc, false, !tri, &b, p, q, pptr, pidx, nullptr);
+        DevBuf<uint8_t> side(usize, s);
+        pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, usize, p, q, side.get(), s);
+        if (st) ++st->flows;
+        // A = source side; S must be a connected component of G[A]
+        LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get());
+        LDS_LAUNCH(side_to_flag_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, side.get(), sc.in.get());
+        // sc.in now marks A; sc.in2 is reused to mark S
+        LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in2.get());
+        LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get(), (int32_t*)nullptr);
+        LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
+        LDS_LAUNCH(component_check_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+                   sc.in2.get(), sc.in.get(), flag.get());
+        LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        result = hflag == 0;
+        LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get());
+        LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get());
+        LDS_CUDA(cudaStreamSynchronize(s));
+        return result;
+    }
+    LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+    LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in2.get());
+    LDS_CUDA(cudaStreamSynchronize(s));
+    return result;
+}
+
+void components(lds_graph* g, const int32_t* list, int32_t k, Scratch& sc, DevBuf<int32_t>& members,
+                std::vector<int32_t>& starts) {
+    cudaStream_t s = g->stream;
+    starts.clear();
+    members.alloc(std::max(k, 1), s);
+    if (k == 0) return;
+    DevBuf<int32_t> label(std::max(g->n, 1), s), changed(1, s);
+    LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), (int32_t*)nullptr);
+    LDS_LAUNCH(cc_init_kernel, grid_for(k, VB), VB, 0, s, list, k, label.get());
+    for (int it = 0;; ++it) {
+        LDS_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
+        LDS_LAUNCH(cc_step_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
+                   sc.in.get(), label.get(), changed.get());
+        int32_t hc = 0;
+        LDS_CUDA(cudaMemcpyAsync(&hc, changed.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        if (!hc) break;
+        LDS_REQUIRE(it <= k + 1, LDS_ETIMEOUT, "components: label propagation did not settle");
+    }
+    LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+    const int bits = std::max(1, bit_length_u64((uint64_t)std::max(g->n, 1)));
+    DevBuf<uint64_t> key(k, s);
+    LDS_LAUNCH(cc_keys_kernel, grid_for(k, VB), VB, 0, s, list, k, label.get(), bits, key.get());
+    radix_sort_u64(key.get(), nullptr, k, 2 * bits, s);
+    DevBuf<int32_t> st(k, s), ns(1, s);
+    LDS_CUDA(cudaMemsetAsync(ns.get(), 0, sizeof(int32_t), s));
+    LDS_LAUNCH(cc_unpack_kernel, grid_for(k, VB), VB, 0, s, key.get(), k, bits, members.get(), st.get(), ns.get());
+    int32_t hn = 0;
+    LDS_CUDA(cudaMemcpyAsync(&hn, ns.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    starts.resize(hn);
+    LDS_CUDA(cudaMemcpyAsync(starts.data(), st.get(), hn * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    std::sort(starts.begin(), starts.end());
+    starts.push_back(k);
+}
+
+lds_graph* subgraph(lds_graph* g, const int32_t* list, int32_t k, Scratch& sc) {
+    cudaStream_t s = g->stream;
+    LDS_LAUNCH(mark_kernel, grid_for(std::max(k, 1), VB), VB, 0, s, list, k, sc.in.get(), sc.local.get());
+    DevBuf<int32_t> cnt(std::max(k, 1), s);
+    DevBuf<int64_t> off;
+    if (k) LDS_LAUNCH(sub_edges_count_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
+                      sc.in.get(), cnt.get());
+    int64_t me = scan_counts(cnt.get(), k, off, s);
+    DevBuf<int32_t> su(std::max<int64_t>(me, 1), s), sv(std::max<int64_t>(me, 1), s);
+    if (k && me)
+        LDS_LAUNCH(sub_edges_fill_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
+                   sc.in.get(), sc.local.get(), off.get(), su.get(), sv.get());
+    LDS_LAUNCH(unmark_kernel, grid_for(std::max(k, 1), VB), VB, 0, s, list, k, sc.in.get());
+    LDS_CUDA(cudaStreamSynchronize(s));
+    lds_graph* h = nullptr;
+    lds_status stt = lds_create_graph(k, me, su.get(), sv.get(), LDS_MEM_DEVICE, s, &h);
+    LDS_REQUIRE(stt == LDS_OK, stt, "subgraph: %s", lds_last_error());
+    return h;
+}
+
+}  // namespace lds

@@ -44,6 +44,18 @@ class FwResult(ctypes.Structure):
                 ("last", ctypes.c_void_p), ("D", ctypes.c_int64)]
 
 
+class LdsResult(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("dens_num", ctypes.POINTER(ctypes.c_int64)),
+                ("dens_den", ctypes.POINTER(ctypes.c_int64)), ("offsets", ctypes.POINTER(ctypes.c_int64)),
+                ("vertices", ctypes.POINTER(ctypes.c_int32))]
+
+
+class TopkStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("fw_rounds", "fw_edge_updates", "certified", "failed", "refined",
+                                              "exact_settled", "skipped_by_bound", "flows", "denser_neighbour")] + \
+               [(f, ctypes.c_double) for f in ("ms_total", "ms_fw", "ms_extract", "ms_prune", "ms_verify")]
+
+
 def _sig(lib, name, res, args):
     fn = getattr(lib, name)
     fn.restype = res
@@ -81,6 +93,10 @@ def load():
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
     _sig(lib, "lds_pattern_max_flow", ctypes.c_int, [i32, i32, P, P, i64, i64, ctypes.POINTER(i64), P])
     _sig(lib, "lds_prune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
+    _sig(lib, "lds_topk", ctypes.c_int, [P, i32, ctypes.c_int, i32, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.POINTER(LdsResult))])
+    _sig(lib, "lds_result_free", None, [ctypes.POINTER(LdsResult)])
+    _sig(lib, "lds_topk_last_stats", ctypes.c_int, [ctypes.POINTER(TopkStats)])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
                                                ctypes.POINTER(i32), P])
     _lib = lib
@@ -143,6 +159,12 @@ def pattern_max_flow(nv: int, patterns, p: int, q: int):
     _check(load().lds_pattern_max_flow(int(nv), len(patterns), _ptr(ptr), _ptr(idx), int(p), int(q),
                                        ctypes.byref(f), _ptr(side)))
     return int(f.value), side[:nv]
+
+
+def topk_last_stats() -> dict:
+    st = TopkStats()
+    _check(load().lds_topk_last_stats(ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in TopkStats._fields_}
 
 
 class Graph:
@@ -242,6 +264,24 @@ class Graph:
                              ctypes.byref(res)))
         out["D"] = int(res.D)
         return out
+
+    def topk(self, k: int, density: str = "edge", iters: int = 100, precision: str = "exact"):
+        """Top-k LDSs (edge) or LTDSs (triangle): list of (Fraction density,
+        int32 array of member ids ascending), densest first."""
+        from fractions import Fraction
+        lib = load()
+        res = ctypes.POINTER(LdsResult)()
+        _check(lib.lds_topk(self._h, int(k), DENSITY[density], int(iters), PRECISION[precision], ctypes.byref(res)))
+        try:
+            r = res.contents
+            out = []
+            for i in range(r.count):
+                a, b = r.offsets[i], r.offsets[i + 1]
+                verts = np.array([r.vertices[j] for j in range(a, b)], dtype=np.int32)
+                out.append((Fraction(r.dens_num[i], r.dens_den[i]), verts))
+            return out
+        finally:
+            lib.lds_result_free(res)
 
     def extract_sg(self):
         """Stable groups (Alg. 2) of the last fw() run on this graph.  Returns a

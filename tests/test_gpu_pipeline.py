@@ -146,3 +146,56 @@ def test_pattern_max_flow_larger_network(lds):
         assert flow == net.max_flow(s, t)
         sw = set(net.maximal_source_side(t))
         assert [int(node[x] in sw) for x in range(n)] == side.tolist()
+
+
+def _as_lists(res):
+    return [(d, [int(x) for x in vs]) for d, vs in res]
+
+
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("triangle", [False, True])
+def test_topk_matches_definition_small(lds, seed, triangle):
+    from oracle import brute
+    n, u, v = synth.gnp_planted(9 + seed % 3, 0.3 + 0.03 * (seed % 6), seed=10000 + seed)[:3]
+    truth = brute.brute_lds(n, u, v, triangle=triangle)
+    dens = "triangle" if triangle else "edge"
+    with lds.Graph(n, u, v) as g:
+        for k in (1, 2, 5):
+            for N, prec in ((3, "exact"), (40, "fp32"), (25, "fp64")):
+                got = _as_lists(g.topk(k, dens, N, prec))
+                assert got == truth[:k], (k, N, prec)
+
+
+def test_topk_fig1(lds):
+    from helpers import load_expected, load_graph, parse_sets
+    n, u, v = load_graph("fig1_graph.txt")
+    exp = load_expected("fig1_expected.txt")
+    with lds.Graph(n, u.astype(np.int32), v.astype(np.int32)) as g:
+        for N in (5, 100):
+            assert _as_lists(g.topk(2, "edge", N)) == parse_sets(exp["lds_top2"])
+            assert _as_lists(g.topk(2, "triangle", N)) == parse_sets(exp["ltds_top2"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_topk_matches_oracle_medium(lds, seed):
+    from oracle import decomp
+    n, u, v, _ = synth.gnp_planted(300, 0.012, (12, 10, 9, 8), (0.9, 0.85, 0.8, 0.9), seed=11000 + seed)
+    truth = decomp.lds_exact(n, u, v)
+    tris = ograph.triangles(n, u, v)
+    truth_t = decomp.ltds_exact(n, u, v, tris)
+    with lds.Graph(n, u, v) as g:
+        assert _as_lists(g.topk(4, "edge", 100)) == [(d, c) for d, c in truth[:4]]
+        assert _as_lists(g.topk(3, "triangle", 100)) == [(d, c) for d, c in truth_t[:3]]
+
+
+def test_topk_planted_gnp_workload(lds):
+    # n = 2000, blocks 20..60: the oracle's driver finishes in seconds here
+    from oracle import ldscvx
+    n, u, v, _ = synth.workload_planted_gnp()
+    want = ldscvx.topk(n, u, v, 5, 200)
+    with lds.Graph(n, u, v) as g:
+        got = _as_lists(g.topk(5, "edge", 200, "fp64"))
+        assert got == want
+        assert _as_lists(g.topk(5, "edge", 200, "exact")) == want
+        stats = lds.topk_last_stats()
+        assert stats["certified"] >= len(want)
