@@ -25,6 +25,8 @@
 //    by Lemma 4 / Lemma 8 lo <= D phi(u) <= hi for u in the group.
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 
 #include "extract_sg.cuh"
 #include "prims.cuh"
@@ -170,9 +172,10 @@ __global__ void cut_list_kernel(const int32_t* flag, const int64_t* excl, int32_
 
 // ---- checks
 
-__global__ void seg_of_pos_kernel(const int64_t* sa, const int64_t* sb, int32_t nseg, int32_t n, int32_t* segof) {
+__global__ void seg_of_pos_kernel(const int64_t* sa, const int64_t* sb, int32_t nseg, int32_t plo, int32_t phi,
+                                  int32_t* segof) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    for (int64_t p = plo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < phi; p += stride) {
         int lo = 0, hi = nseg;            // last segment with sa <= p
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
@@ -228,7 +231,7 @@ __global__ void check_edges_kernel(const int32_t* order, const int32_t* pos, con
                     push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)y, share_x);
                 }
             }
-            if (!count_only) deltaS[p] = d;
+            if (!count_only) deltaS[p - npos_lo] = d;
         }
     }
 }
@@ -274,7 +277,7 @@ __global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, cons
                 int64_t w = W[3 * (int64_t)t + k];
                 moved += w;
                 if (pp[k] >= a && pp[k] <= b) {
-                    if (!count_only) atomicAdd(deltaS + pp[k], (unsigned long long)(-w));
+                    if (!count_only) atomicAdd(deltaS + (pp[k] - npos_lo), (unsigned long long)(-w));
                 } else if (count_only) {
                     atomicAdd(rec.count, 1ull);
                 } else {
@@ -282,7 +285,7 @@ __global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, cons
                 }
             }
             if (pp[tgt] >= a && pp[tgt] <= b) {
-                if (!count_only) atomicAdd(deltaS + pp[tgt], (unsigned long long)moved);
+                if (!count_only) atomicAdd(deltaS + (pp[tgt] - npos_lo), (unsigned long long)moved);
             } else if (count_only) {
                 atomicAdd(rec.count, 1ull);
             } else {
@@ -295,6 +298,11 @@ __global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, cons
 __global__ void iota_u32_kernel(uint32_t* p, int64_t k) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) p[i] = (uint32_t)i;
+}
+
+__global__ void fill_i32_range_kernel(int32_t* p, int32_t lo, int32_t hi, int32_t v) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += stride) p[i] = v;
 }
 
 __global__ void rec_gather_vals_kernel(const int64_t* val, const uint32_t* idx, int64_t k, int64_t* out) {
@@ -324,7 +332,7 @@ __global__ void side_s_kernel(const int32_t* order, const int32_t* segof, int32_
     for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
         int32_t s = segof[p];
         if (s < 0) continue;
-        long long v = (long long)(R[order[p]] + deltaS[p]);
+        long long v = (long long)(R[order[p]] + deltaS[p - npos_lo]);
         atomicMin(minS + s, v);
         atomicMax(maxS + s, v);
     }
@@ -396,7 +404,8 @@ void ensure_vertex_triangles(lds_graph* g) {
 
 // Checks the given disjoint segments (positions, inclusive) and returns
 // (minS, maxS, minX, maxZ) per segment.
-static void check_segments(lds_graph* g, const SgState& st, const std::vector<int64_t>& ha,
+// segof (device, all -1 between calls) maps positions to checked segments.
+static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, const std::vector<int64_t>& ha,
                            const std::vector<int64_t>& hb, std::vector<long long>& minS, std::vector<long long>& maxS,
                            std::vector<long long>& minX, std::vector<long long>& maxZ) {
     cudaStream_t s = g->stream;
@@ -408,10 +417,9 @@ static void check_segments(lds_graph* g, const SgState& st, const std::vector<in
     copy_in(sa.get(), ha.data(), LDS_MEM_HOST, nseg * sizeof(int64_t), s);
     copy_in(sb.get(), hb.data(), LDS_MEM_HOST, nseg * sizeof(int64_t), s);
     const int32_t plo = (int32_t)ha.front(), phi = (int32_t)hb.back() + 1;
-    DevBuf<int32_t> segof(n, s);
-    LDS_LAUNCH(seg_of_pos_kernel, grid_for(n, blk), blk, 0, s, sa.get(), sb.get(), nseg, n, segof.get());
-    DevBuf<int64_t> deltaS(n, s);
-    LDS_CUDA(cudaMemsetAsync(deltaS.get(), 0, n * sizeof(int64_t), s));
+    LDS_LAUNCH(seg_of_pos_kernel, grid_for(phi - plo, blk), blk, 0, s, sa.get(), sb.get(), nseg, plo, phi, segof);
+    DevBuf<int64_t> deltaS(phi - plo, s);
+    LDS_CUDA(cudaMemsetAsync(deltaS.get(), 0, (phi - plo) * sizeof(int64_t), s));
     DevBuf<unsigned long long> rcnt(1, s);
     const int64_t* W = g->fw_W.get();
     const int32_t nact = g->nact;
@@ -435,12 +443,12 @@ static void check_segments(lds_graph* g, const SgState& st, const std::vector<in
             if (g->m) {
                 ensure_slot_edge(g);
                 LDS_LAUNCH(check_edges_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(),
-                           segof.get(), sa.get(), sb.get(), plo, phi, g->rowptr.get(), g->col.get(), g->slot_edge.get(),
+                           segof, sa.get(), sb.get(), plo, phi, g->rowptr.get(), g->col.get(), g->slot_edge.get(),
                            g->eu.get(), W, g->fw_D, n, nact, deltaS.get(), rec, count_only);
             }
         } else if (g->ntri) {
             ensure_vertex_triangles(g);
-            LDS_LAUNCH(check_tris_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(), segof.get(),
+            LDS_LAUNCH(check_tris_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(), segof,
                        sa.get(), sb.get(), plo, phi, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(), g->tb.get(),
                        g->tc.get(), W, n, nact, (unsigned long long*)deltaS.get(), rec, count_only);
         }
@@ -464,8 +472,9 @@ static void check_segments(lds_graph* g, const SgState& st, const std::vector<in
         LDS_LAUNCH(rec_reduce_kernel, grid_for((int64_t)nrec, blk), blk, 0, s, rkey.get(), sval.get(), (int64_t)nrec, n,
                    g->fw_R.get(), st.pos.get(), sa.get(), dminX.get(), dmaxZ.get());
     }
-    LDS_LAUNCH(side_s_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), segof.get(), plo, phi, g->fw_R.get(),
+    LDS_LAUNCH(side_s_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), segof, plo, phi, g->fw_R.get(),
                deltaS.get(), dminS.get(), dmaxS.get());
+    LDS_LAUNCH(fill_i32_range_kernel, grid_for(phi - plo, blk), blk, 0, s, segof, plo, phi, -1);
     minS.resize(nseg);
     maxS.resize(nseg);
     minX.resize(nseg);
@@ -548,39 +557,40 @@ void extract_sg(lds_graph* g, SgState& st) {
         cb.push_back(c - 1);
         prev = c;
     }
+    DevBuf<int32_t> segof(n, s);
+    LDS_LAUNCH(fill_i32_range_kernel, grid_for(n, blk), blk, 0, s, segof.get(), 0, n, -1);
     std::vector<long long> mnS, mxS, mnX, mxZ;
-    check_segments(g, st, ca, cb, mnS, mxS, mnX, mxZ);
-    auto passes = [&](size_t i, int64_t a, int64_t b) {
-        bool ok = true;
-        if (a > 0) ok &= mnX[i] > mxS[i];
-        if (b < n - 1) ok &= mxZ[i] < mnS[i];
-        return ok;
-    };
+    check_segments(g, st, segof.get(), ca, cb, mnS, mxS, mnX, mxZ);
+    // For a fixed start, growing the segment only lowers the X vertices' modified
+    // loads and only raises max_S r': once the X-side test fails it fails for
+    // every longer merge, so the whole rest is the unaccepted remainder.
     int64_t start = 0;
     for (size_t k = 0; k < ca.size(); ++k) {
-        long long lo, hi;
-        bool ok;
+        long long lo, hi, mx, mz;
         if (ca[k] == start) {
-            ok = passes(k, ca[k], cb[k]);
-            lo = mnS[k];
-            hi = mxS[k];
+            lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
             std::vector<int64_t> a1{start}, b1{cb[k]};
             std::vector<long long> s1, s2, s3, s4;
-            check_segments(g, st, a1, b1, s1, s2, s3, s4);
-            ok = true;
-            if (start > 0) ok &= s3[0] > s2[0];
-            if (cb[k] < n - 1) ok &= s4[0] < s1[0];
-            lo = s1[0];
-            hi = s2[0];
+            check_segments(g, st, segof.get(), a1, b1, s1, s2, s3, s4);
+            lo = s1[0]; hi = s2[0]; mx = s3[0]; mz = s4[0];
+            ++st.chain_checks;
         }
-        if (ok) {
+        const bool xok = start == 0 || mx > hi;
+        const bool zok = cb[k] == n - 1 || mz < lo;
+        if (xok && zok) {
             st.group_end.push_back(cb[k] + 1);
             st.lo.push_back(lo);
             st.hi.push_back(hi);
             start = cb[k] + 1;
+        } else if (!xok) {
+            break;
         }
     }
+    const char* vb = getenv("LDS_VERBOSE");
+    if (vb && vb[0] == '1')
+        fprintf(stderr, "[extract_sg] n=%d candidates=%zu groups=%zu chain_checks=%lld\n", n, ca.size(),
+                st.group_end.size(), (long long)st.chain_checks);
 }
 
 }  // namespace lds

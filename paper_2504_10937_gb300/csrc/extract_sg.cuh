@@ -14,6 +14,7 @@ struct SgState {
     std::vector<int64_t> cuts;            // 1-based cut positions (ascending)
     std::vector<int64_t> group_end;       // exclusive end position of each accepted group
     std::vector<long long> lo, hi;        // min / max modified load of each group (over D)
+    int64_t chain_checks = 0;             // single checks of merged candidates
 };
 
 // Alg. 2 on the last Frank-Wolfe run of g (g->fw_*).

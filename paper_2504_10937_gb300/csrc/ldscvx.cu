@@ -18,6 +18,8 @@
 //   * Output: density descending, ties by smallest member id.
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -439,6 +441,9 @@ void Driver::exact_settle(const int32_t* comp, int32_t csize) {
 
 void Driver::run() {
     auto T0 = std::chrono::steady_clock::now();
+    const char* vb = getenv("LDS_VERBOSE");
+    const bool verbose = vb && vb[0] == '1';
+    auto elapsed = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - T0).count(); };
     cudaStream_t s = st();
     if (tri) ensure_triangles(G);
     init_bounds(G, bG);
@@ -453,11 +458,19 @@ void Driver::run() {
     auto mshared = std::make_shared<DevBuf<int32_t>>(std::move(members));
     for (size_t gidx = offs.size() - 1; gidx-- > 0;)
         stack.push_back({mshared, offs[gidx], offs[gidx + 1] - offs[gidx]});
+    if (verbose)
+        fprintf(stderr, "[lds_topk] first round done at %.3fs: %zu groups\n", elapsed(), stack.size());
+    int64_t popped = 0;
     while (!stack.empty()) {
         Item it = stack.back();
         stack.pop_back();
         const int32_t* S = it.buf->get() + it.off;
         const int32_t ssz = (int32_t)it.size;
+        ++popped;
+        if (verbose && (popped < 50 || popped % 1000 == 0))
+            fprintf(stderr, "[lds_topk] %.3fs pop #%lld size %d stack %zu found %zu refined %lld flows %lld\n",
+                    elapsed(), (long long)popped, ssz, stack.size(), found.size(), (long long)stats.refined,
+                    (long long)vst.flows);
         int64_t rkn, rkd;
         if (kth(rkn, rkd)) {
             DevBuf<int32_t> flag(1, s);
