@@ -1,15 +1,19 @@
-"""Benchmark: Frank-Wolfe edge-updates per second on the power-law workload.
+"""Benchmark: Frank-Wolfe edge-updates per second and top-k LDS queries per
+second on the power-law workload.
 
 Workload: Chung-Lu graph with n = 1,000,000 vertices, 10,000,000 background
 edges (degree exponent 2.1) plus 50 planted blocks of log-uniform size 50-500
-and edge probability U(0.3, 0.9) (about 10.8M edges in all), delivered as a raw
+and edge probability U(0.3, 0.9) (about 10.6M edges in all), delivered as a raw
 edge list (random orientation and order, 5% repeated pairs, 1% self-loops)
 already resident in device memory.
 
-One step = one pass of the path on that input: graph ingest (canonical edges +
-CSR) followed by 500 Frank-Wolfe iterations (Alg. 1) in the chosen
-arithmetic.  value = edge-updates (m * iterations) / step time.  L2 is flushed
-between steps (a 512 MiB device write outside the per-step events).
+One step = one top-10 LDS query over that input through the library: graph
+ingest (canonical edges + CSR), initial reduction, Frank-Wolfe (Alg. 1, 500
+iterations per round), ExtractSG, Pruning, IsDensest / IsLDS max-flow
+verification and the refinement rounds of the driver.  value = Frank-Wolfe
+edge-updates executed in the step / step time (whole step, not only the FW
+kernels; the FW-only rate is reported beside it).  L2 is flushed between steps
+(a 512 MiB device write outside the per-step events).
 
 ``--impl reference`` times the CPU oracle (oracle.fw) on the host cores on a
 bounded number of iterations of the same graph and reports the same metric.
@@ -162,9 +166,9 @@ def run_reference(args):
 
 def _config(args, n, m):
     return {"workload": "chung_lu_n1e6_m1e7_exp2.1_50blocks (seed 2), raw COO with 5% repeats and 1% self-loops",
-            "n": n, "m": m, "iters": args.iters, "precision": args.precision, "density": "edge",
-            "step": "ingest + Frank-Wolfe", "l2": "flushed between steps (512 MiB device write)",
-            "parallelism": f"replicas x{args.gpus}"}
+            "n": n, "m": m, "iters": args.iters, "precision": args.precision, "density": "edge", "k": args.k,
+            "step": "ingest + Frank-Wolfe" if getattr(args, "fw_only", False) else "top-k LDS query (lds_topk)",
+            "l2": "flushed between steps (512 MiB device write)", "parallelism": f"replicas x{args.gpus}"}
 
 
 def cpu_baseline(n, u, v, budget_s=12.0):
@@ -205,9 +209,15 @@ def run_ours(args):
     def step():
         g = lds.Graph(n, ta, tb, stream=sptr)
         m_holder["m"] = g.m
-        g.fw(args.iters, precision=args.precision, want=())
+        if args.fw_only:
+            g.fw(args.iters, precision=args.precision, want=())
+            st = {"fw_edge_updates": g.m * args.iters}
+        else:
+            m_holder["result"] = g.topk(args.k, "edge", args.iters, args.precision)
+            st = lds.topk_last_stats()
         t = g.fw_timing()
         g.close()
+        t["stats"] = st
         return t
 
     for _ in range(args.warmup):
@@ -215,7 +225,7 @@ def run_ours(args):
         flush.zero_()
     torch.cuda.synchronize()
     lds.set_pass_profiling(True)
-    times, pass_us, fw_ms = [], [], []
+    times, pass_us, fw_ms, updates, phase = [], [], [], [], []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -231,6 +241,8 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1))
             pass_us.append(t["pass_us"])
             fw_ms.append(t["fw_ms"])
+            updates.append(t["stats"]["fw_edge_updates"])
+            phase.append(t["stats"])
             last_timing = t
             flush.zero_()
         torch.cuda.synchronize()
@@ -244,7 +256,7 @@ def run_ours(args):
         tt = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
-    units = m * args.iters * args.steps * world
+    units = sum(updates) * world
     value = units / (total_ms / 1000.0)
 
     # end to end through the C-ABI with host (pinned) buffers
@@ -255,13 +267,35 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g = lds.Graph(n, ha.numpy(), hb.numpy(), stream=sptr)
-        out = g.fw(args.iters, precision=args.precision, want=("r",))
+        if args.fw_only:
+            g.fw(args.iters, precision=args.precision, want=("r",))
+            e2e_updates = g.m * args.iters
+        else:
+            g.topk(args.k, "edge", args.iters, args.precision)
+            e2e_updates = lds.topk_last_stats()["fw_edge_updates"]
         g.close()
         dt = time.perf_counter() - t0
         if k:
             e2e_times.append(dt)
         flush.zero_()
-    e2e_value = m * args.iters / statistics.mean(e2e_times) if e2e_times else None
+    e2e_value = e2e_updates / statistics.mean(e2e_times) if e2e_times else None
+
+    # the plain single-graph binary64 GPU path (Alg. 1 literally) on the same query
+    plain = None
+    if not args.fw_only and not args.no_plain:
+        pt = []
+        for k in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = lds.Graph(n, ta, tb, stream=sptr)
+            g.topk(args.k, "edge", args.iters, "fp64")
+            g.close()
+            torch.cuda.synchronize()
+            if k:
+                pt.append(time.perf_counter() - t0)
+            flush.zero_()
+        plain = {"precision": "fp64 (Alg. 1 literal, symmetric slots)", "queries_per_s": 1.0 / statistics.mean(pt),
+                 "ms_per_query": 1000.0 * statistics.mean(pt)}
 
     hbm, peak_kind = _peaks()
     bytes_per_pass = last_timing["pass_bytes"]
@@ -276,7 +310,13 @@ def run_ours(args):
             "dtype": {"exact": "int64", "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic", "config": _config(args, n, m),
             "fw_only": {"value": m * args.iters / (statistics.mean(fw_ms) / 1000.0), "unit": UNIT,
-                        "fw_ms": statistics.mean(fw_ms)},
+                        "fw_ms": statistics.mean(fw_ms), "note": "first-round FW kernels on G only"},
+            "queries_per_s": None if args.fw_only else 1000.0 * args.steps / total_ms,
+            "plain_fp64_gpu": plain,
+            "phases_ms": None if args.fw_only else {k: statistics.mean(p[k] for p in phase)
+                                                     for k in ("ms_total", "ms_fw", "ms_extract", "ms_prune",
+                                                               "ms_verify")},
+            "result": None if args.fw_only else [[str(d), len(c)] for d, c in m_holder["result"]],
             "roofline": {"bound": "hbm", "kernel": last_timing["pass_kernel"], "achieved": achieved, "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                          "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_us": avg_pass_us},
@@ -301,6 +341,9 @@ def main():
     ap.add_argument("--iters", type=int, default=500)
     ap.add_argument("--precision", choices=["exact", "fp32", "fp64"], default="exact")
     ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--fw-only", action="store_true", help="time ingest + FW only (profiling runs)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the binary64 comparison queries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     args = ap.parse_args()
