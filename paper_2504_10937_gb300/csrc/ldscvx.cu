@@ -503,11 +503,20 @@ void Driver::run() {
             int64_t npat = 0;
             auto tv1 = std::chrono::steady_clock::now();
             bool dens = is_densest(G, tri, comp, csize, sc, &npat);
+            auto tv2 = std::chrono::steady_clock::now();
             if (dens) {
                 certify(comp, csize, npat);
-                tm.verify += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv1).count();
+                auto tv3 = std::chrono::steady_clock::now();
+                tm.verify += std::chrono::duration<double, std::milli>(tv3 - tv1).count();
+                if (verbose && csize > 2)
+                    fprintf(stderr, "[lds_topk]   component %d (|P|=%lld): densest %.1f ms, certify %.1f ms\n", csize,
+                            (long long)npat, std::chrono::duration<double, std::milli>(tv2 - tv1).count(),
+                            std::chrono::duration<double, std::milli>(tv3 - tv2).count());
                 continue;
             }
+            if (verbose)
+                fprintf(stderr, "[lds_topk]   component %d (|P|=%lld): not densest %.1f ms\n", csize, (long long)npat,
+                        std::chrono::duration<double, std::milli>(tv2 - tv1).count());
             tm.verify += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv1).count();
             // refine on G[comp]
             int32_t n_try = N;

@@ -9,6 +9,9 @@
 // set in which every vertex's core number reaches its lower bound (core numbers
 // only grow with the graph), whatever the removal order, so removing all
 // violators of a round at once is the same as Alg. 3's one-at-a-time loop.
+#include <cstdio>
+#include <cstdlib>
+
 #include "prune.cuh"
 
 namespace lds {
@@ -81,6 +84,8 @@ void prune(lds_graph* g, bool tri, const int64_t* ubn, const int64_t* ubd, const
         int32_t hr = 0;
         LDS_CUDA(cudaMemcpyAsync(&hr, removed.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
+        const char* vb = getenv("LDS_VERBOSE");
+        if (vb && vb[0] == '1') fprintf(stderr, "[prune] n=%d round %d removed %d\n", n, round, hr);
         if (hr == 0) break;
         LDS_REQUIRE(round < n + 1, LDS_ETIMEOUT, "prune: rule 2 did not settle");
     }

@@ -14,8 +14,12 @@
 // vertex is removed; then k moves to the smallest remaining degree.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "graph.cuh"
 #include "prims.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lds {
 
@@ -238,6 +242,77 @@ __global__ void alive_tri_count_kernel(const int32_t* ta, const int32_t* tb, con
     }
 }
 
+// Whole peeling loop in one cooperative launch.  ctrl: [0] frontier size,
+// [1] vertices left, [2] smallest live degree, [3] error (iteration bound hit).
+// Every thread follows the same k and the same branches: the counters are
+// read right after a grid-wide barrier.
+__global__ void peel_coop_kernel(int32_t nact, bool tri, const int64_t* rowptr, const int32_t* col, const int64_t* vptr,
+                                 const int32_t* vtri, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                 uint8_t* tdead, uint8_t* alive, int32_t* deg, int64_t* core, int32_t* frontier,
+                                 unsigned long long* ctrl, int64_t max_steps) {
+    cg::grid_group grid = cg::this_grid();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    int64_t k = 0;
+    for (int64_t step = 0;; ++step) {
+        if (step >= max_steps) {
+            if (tid == 0) ctrl[3] = 1;
+            return;
+        }
+        for (int64_t x = tid; x < nact; x += nthreads) {
+            if (!__ldcg(alive + x)) continue;
+            int32_t d = __ldcg(deg + x);
+            if (d <= k) {
+                alive[x] = 0;
+                core[x] = k;
+                frontier[atomicAdd(ctrl, 1ull)] = (int32_t)x;
+            } else {
+                atomicMin(ctrl + 2, (unsigned long long)d);
+            }
+        }
+        grid.sync();
+        const unsigned long long f = __ldcg(ctrl);
+        const unsigned long long left = __ldcg(ctrl + 1);
+        const unsigned long long mn = __ldcg(ctrl + 2);
+        grid.sync();
+        if (f == 0) {
+            if (left == 0) return;
+            k = max(k + 1, (int64_t)mn);
+            if (tid == 0) ctrl[2] = ~0ull;
+            grid.sync();
+            continue;
+        }
+        for (int64_t i = tid; i < (int64_t)f; i += nthreads) {
+            int32_t x = __ldcg(frontier + i);
+            if (!tri) {
+                for (int64_t s = rowptr[x], e = rowptr[x + 1]; s < e; ++s) {
+                    int32_t y = col[s];
+                    if (__ldcg(alive + y)) atomicSub(deg + y, 1);
+                }
+            } else {
+                for (int64_t s = vptr[x], e = vptr[x + 1]; s < e; ++s) {
+                    int32_t t = vtri[s];
+                    unsigned int* word = (unsigned int*)(tdead + (t & ~3));
+                    unsigned int bit = 1u << (8 * (t & 3));
+                    if (atomicOr(word, bit) & bit) continue;
+                    int32_t a = ta[t], b = tb[t], c = tc[t];
+                    if (a != x && __ldcg(alive + a)) atomicSub(deg + a, 1);
+                    if (b != x && __ldcg(alive + b)) atomicSub(deg + b, 1);
+                    if (c != x && __ldcg(alive + c)) atomicSub(deg + c, 1);
+                }
+            }
+        }
+        grid.sync();
+        if (tid == 0) {
+            ctrl[1] = left - f;
+            ctrl[0] = 0;
+            ctrl[2] = ~0ull;
+        }
+        grid.sync();
+        if (left - f == 0) return;
+    }
+}
+
 __global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < to; x += stride) p[x] = v;
@@ -331,33 +406,39 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     int32_t remaining = 0;
     LDS_CUDA(cudaMemcpyAsync(&remaining, nalive.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
-    int64_t k = 0;
-    int64_t guard_steps = 0;
-    while (remaining > 0) {
-        LDS_CUDA(cudaMemsetAsync(fcount.get(), 0, sizeof(int32_t), s));
-        int64_t big = INT64_MAX;
-        LDS_CUDA(cudaMemcpyAsync(minalive.get(), &big, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-        LDS_LAUNCH(peel_select_kernel, grid_for(nact, blk), blk, 0, s, deg.get(), alive.get(), nact, k, core_int,
-                   frontier.get(), fcount.get(), minalive.get());
-        int32_t hf = 0;
-        int64_t hmin = 0;
-        LDS_CUDA(cudaMemcpyAsync(&hf, fcount.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        LDS_CUDA(cudaMemcpyAsync(&hmin, minalive.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        LDS_CUDA(cudaStreamSynchronize(s));
-        if (hf == 0) {
-            // nothing at this level: jump to the smallest live degree
-            k = std::max<int64_t>(k + 1, hmin);
-            continue;
-        }
-        remaining -= hf;
-        if (!tri)
-            LDS_LAUNCH(peel_edges_kernel, grid_for(hf, 128), 128, 0, s, g->rowptr.get(), g->col.get(), frontier.get(), hf,
-                       alive.get(), deg.get());
-        else
-            LDS_LAUNCH(peel_tris_kernel, grid_for(hf, 128), 128, 0, s, g->vt_ptr.get(), g->vt_idx.get(), frontier.get(),
-                       hf, g->ta.get(), g->tb.get(), g->tc.get(), tdead.get(), alive.get(), deg.get());
-        LDS_REQUIRE(++guard_steps < 4 * (int64_t)nact + 16, LDS_ETIMEOUT, "core numbers: peeling did not finish");
-    }
+    if (remaining == 0) return;
+    // one cooperative launch runs every level; the grid must be resident at once
+    DevBuf<unsigned long long> ctrl(4, s);
+    unsigned long long hctrl[4] = {0ull, (unsigned long long)remaining, ~0ull, 0ull};
+    LDS_CUDA(cudaMemcpyAsync(ctrl.get(), hctrl, sizeof(hctrl), cudaMemcpyHostToDevice, s));
+    int dev = 0, per_sm = 0;
+    LDS_CUDA(cudaGetDevice(&dev));
+    LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_coop_kernel, blk, 0));
+    LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "core numbers: peeling kernel cannot be resident");
+    int grid = std::max(1, std::min(per_sm * num_sms(), (int)((nact + blk - 1) / blk)));
+    const int64_t max_steps = 4 * (int64_t)nact + 64;
+    const bool trib = tri;
+    const int64_t* rp = g->rowptr.get();
+    const int32_t* cl = g->col.get();
+    const int64_t* vp = tri ? g->vt_ptr.get() : nullptr;
+    const int32_t* vi = tri ? g->vt_idx.get() : nullptr;
+    const int32_t* pa = tri ? g->ta.get() : nullptr;
+    const int32_t* pb = tri ? g->tb.get() : nullptr;
+    const int32_t* pc = tri ? g->tc.get() : nullptr;
+    uint8_t* td = tri ? tdead.get() : nullptr;
+    uint8_t* al = alive.get();
+    int32_t* dg = deg.get();
+    int32_t* fr = frontier.get();
+    unsigned long long* ct = ctrl.get();
+    int32_t nact_ = nact;
+    void* args[] = {&nact_, (void*)&trib, (void*)&rp, (void*)&cl, (void*)&vp, (void*)&vi, (void*)&pa, (void*)&pb,
+                    (void*)&pc, (void*)&td, (void*)&al, (void*)&dg, (void*)&core_int, (void*)&fr, (void*)&ct,
+                    (void*)&max_steps};
+    LDS_CUDA(cudaLaunchCooperativeKernel((void*)peel_coop_kernel, dim3(grid), dim3(blk), args, 0, s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    LDS_CUDA(cudaMemcpyAsync(hctrl, ctrl.get(), sizeof(hctrl), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    LDS_REQUIRE(hctrl[3] == 0, LDS_ETIMEOUT, "core numbers: peeling hit its iteration bound");
 }
 
 void core_numbers(lds_graph* g, bool tri, int64_t* core_int_out, const uint8_t* init_alive) {

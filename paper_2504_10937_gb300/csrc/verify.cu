@@ -482,7 +482,10 @@ bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch&
     int64_t np = build_patterns(g, tri, list, k, sc, true, false, nullptr, 0, 1, pptr, pidx, nullptr);
     *npat = np;
     bool ok = true;
-    if (np > 0) {
+    // a connected edge set with |E| = |S| - 1 is a tree: every proper subset has
+    // density (j - 1) / j or less, so it is its own densest subgraph
+    const bool tree = !tri && np == (int64_t)k - 1;
+    if (np > 0 && !tree) {
         int64_t gg = gcd64(np, k);
         int64_t p = np / gg, q = k / gg;
         int64_t f = pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, k, p, q, nullptr, s);
