@@ -185,12 +185,14 @@ lds_status lds_prune(lds_graph* g, lds_density d, const int64_t* ub_num, const i
  * scaled by q.  GPU push-relabel.
  *   nv, np            vertices and patterns
  *   pat_ptr[np + 1], pat_idx[pat_ptr[np]]  host arrays: pattern j lists vertices
- *                     pat_idx[pat_ptr[j] .. pat_ptr[j+1]) (indices in [0, nv))
+ *                     pat_idx[pat_ptr[j] .. pat_ptr[j+1]) (indices in [0, nv),
+ *                     distinct within a pattern; pat_ptr[0] = 0)
  *   flow              output: maximum flow value
  *   source_side[nv]   output (may be NULL): 1 for vertices on the largest source
  *                     side of a minimum cut (those that cannot reach the sink in
  *                     the final residual network; Lemma 9's cut)
- * Errors: LDS_EINVAL, LDS_ETIMEOUT (iteration bound), LDS_ENOMEM, LDS_ECUDA. */
+ * Errors: LDS_EINVAL, LDS_ETIMEOUT (iteration bound), LDS_EOVERFLOW (np q above
+ * 2^62), LDS_ENOMEM, LDS_ECUDA. */
 lds_status lds_pattern_max_flow(int32_t nv, int32_t np, const int64_t* pat_ptr, const int32_t* pat_idx, int64_t p,
                                 int64_t q, int64_t* flow, uint8_t* source_side);
 

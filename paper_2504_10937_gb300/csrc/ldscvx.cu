@@ -376,7 +376,7 @@ void Driver::exact_settle(const int32_t* comp, int32_t csize) {
         if (p == 0) q = 1;
         std::vector<uint8_t> X(nf, 1);
         for (int it = 0;; ++it) {
-            int64_t f = pattern_max_flow(dptr.get(), ridx.get(), (int32_t)nr, nf, p, q, side.get(), s);
+            int64_t f = pattern_max_flow(dptr.get(), ridx.get(), (int32_t)nr, nf, p, q, nullptr, side.get(), false, s);
             ++vst.flows;
             int64_t value = q * nr - f;
             std::vector<uint8_t> hs(nf);
@@ -447,9 +447,12 @@ void Driver::run() {
     cudaStream_t s = st();
     if (tri) ensure_triangles(G);
     init_bounds(G, bG);
+    if (verbose) fprintf(stderr, "[lds_topk] initial bounds at %.3fs\n", elapsed());
     DevBuf<int32_t> members;
     std::vector<int64_t> offs;
     round(G, bG, N, members, offs);
+    if (verbose)
+        fprintf(stderr, "[lds_topk] first round: fw %.1f ms, extract %.1f ms, prune %.1f ms\n", tm.fw, tm.sg, tm.prune);
     struct Item {
         std::shared_ptr<DevBuf<int32_t>> buf;
         int64_t off, size;
@@ -496,13 +499,28 @@ void Driver::run() {
         std::vector<int32_t> cs;
         auto tv0 = std::chrono::steady_clock::now();
         components(G, sorted.get(), ssz, sc, cm, cs);
+        if (verbose)
+            fprintf(stderr, "[lds_topk]   %zu components in %.1f ms\n", cs.size() - 1,
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv0).count());
+        double small_ms = 0;
+        int small_n = 0;
         auto cmh = std::make_shared<DevBuf<int32_t>>(std::move(cm));
         for (size_t c = 0; c + 1 < cs.size(); ++c) {
             const int32_t* comp = cmh->get() + cs[c];
             const int32_t csize = cs[c + 1] - cs[c];
             int64_t npat = 0;
             auto tv1 = std::chrono::steady_clock::now();
-            bool dens = is_densest(G, tri, comp, csize, sc, &npat);
+            // a connected set of one vertex (of two, for triangles) holds no pattern: density 0,
+            // never reported; a connected pair is one edge, its own densest subgraph
+            const bool trivial = csize == 1 || csize == 2;
+            if (trivial && (csize == 1 || tri) && !include_zero) continue;
+            bool dens;
+            if (trivial) {
+                npat = (csize == 2 && !tri) ? 1 : 0;
+                dens = true;
+            } else {
+                dens = is_densest(G, tri, comp, csize, sc, &npat);
+            }
             auto tv2 = std::chrono::steady_clock::now();
             if (dens) {
                 certify(comp, csize, npat);
@@ -512,6 +530,10 @@ void Driver::run() {
                     fprintf(stderr, "[lds_topk]   component %d (|P|=%lld): densest %.1f ms, certify %.1f ms\n", csize,
                             (long long)npat, std::chrono::duration<double, std::milli>(tv2 - tv1).count(),
                             std::chrono::duration<double, std::milli>(tv3 - tv2).count());
+                if (csize <= 2) {
+                    small_ms += std::chrono::duration<double, std::milli>(tv3 - tv1).count();
+                    ++small_n;
+                }
                 continue;
             }
             if (verbose)
@@ -553,7 +575,12 @@ void Driver::run() {
                 }
                 n_try *= 2;
             }
+            if (verbose)
+                fprintf(stderr, "[lds_topk]   refined component %d in %.1f ms\n", csize,
+                        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv2).count());
         }
+        if (verbose && small_n)
+            fprintf(stderr, "[lds_topk]   %d components of size <= 2 verified in %.1f ms\n", small_n, small_ms);
         tm.refine += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv0).count();
     }
     stats.flows = vst.flows;

@@ -131,52 +131,6 @@ __global__ void tri_rows_orig_kernel(const int32_t* ta, const int32_t* tb, const
 
 // ---- peeling
 
-__global__ void peel_select_kernel(const int32_t* deg, uint8_t* alive, int32_t nact, int64_t k, int64_t* core,
-                                   int32_t* frontier, int32_t* fcount, int64_t* min_alive) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride) {
-        if (!alive[x]) continue;
-        if (deg[x] <= k) {
-            alive[x] = 0;
-            core[x] = k;
-            frontier[atomicAdd(fcount, 1)] = (int32_t)x;
-        } else {
-            atomicMin((unsigned long long*)min_alive, (unsigned long long)deg[x]);
-        }
-    }
-}
-
-__global__ void peel_edges_kernel(const int64_t* rowptr, const int32_t* col, const int32_t* frontier, int32_t fcount,
-                                  const uint8_t* alive, int32_t* deg) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += stride) {
-        int32_t x = frontier[i];
-        for (int64_t s = rowptr[x], e = rowptr[x + 1]; s < e; ++s) {
-            int32_t y = col[s];
-            if (alive[y]) atomicSub(deg + y, 1);
-        }
-    }
-}
-
-__global__ void peel_tris_kernel(const int64_t* vptr, const int32_t* vtri, const int32_t* frontier, int32_t fcount,
-                                 const int32_t* ta, const int32_t* tb, const int32_t* tc, uint8_t* tdead,
-                                 const uint8_t* alive, int32_t* deg) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += stride) {
-        int32_t x = frontier[i];
-        for (int64_t s = vptr[x], e = vptr[x + 1]; s < e; ++s) {
-            int32_t t = vtri[s];
-            unsigned int* word = (unsigned int*)(tdead + (t & ~3));
-            unsigned int bit = 1u << (8 * (t & 3));
-            unsigned int old = atomicOr(word, bit);
-            if (old & bit) continue;
-            int32_t a = ta[t], b = tb[t], c = tc[t];
-            if (a != x && alive[a]) atomicSub(deg + a, 1);
-            if (b != x && alive[b]) atomicSub(deg + b, 1);
-            if (c != x && alive[c]) atomicSub(deg + c, 1);
-        }
-    }
-}
 
 __global__ void degree_kernel(const int64_t* rowptr, int32_t nact, int32_t* deg) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -242,75 +196,164 @@ __global__ void alive_tri_count_kernel(const int32_t* ta, const int32_t* tb, con
     }
 }
 
-// Whole peeling loop in one cooperative launch.  ctrl: [0] frontier size,
-// [1] vertices left, [2] smallest live degree, [3] error (iteration bound hit).
-// Every thread follows the same k and the same branches: the counters are
-// read right after a grid-wide barrier.
-__global__ void peel_coop_kernel(int32_t nact, bool tri, const int64_t* rowptr, const int32_t* col, const int64_t* vptr,
-                                 const int32_t* vtri, const int32_t* ta, const int32_t* tb, const int32_t* tc,
-                                 uint8_t* tdead, uint8_t* alive, int32_t* deg, int64_t* core, int32_t* frontier,
-                                 unsigned long long* ctrl, int64_t max_steps) {
+// Removes one peeled vertex x at level k: every live neighbour (edge) or
+// every other vertex of each live triangle of x loses one; a vertex whose
+// count falls from k + 1 to k is peeled at level k too (exactly one decrement
+// sees k + 1) and joins the next frontier.
+__device__ __forceinline__ void peel_drop(int32_t y, int64_t k, uint8_t* alive, int32_t* deg, int64_t* core,
+                                          int32_t* next, unsigned long long* next_cnt) {
+    if (!__ldcg(alive + y)) return;
+    if ((int64_t)atomicSub(deg + y, 1) == k + 1) {
+        alive[y] = 0;
+        core[y] = k;
+        next[atomicAdd(next_cnt, 1ull)] = y;
+    }
+}
+
+__device__ __forceinline__ void peel_triangle(int32_t t, int32_t x, int64_t k, const int32_t* ta, const int32_t* tb,
+                                              const int32_t* tc, uint8_t* tdead, uint8_t* alive, int32_t* deg,
+                                              int64_t* core, int32_t* next, unsigned long long* next_cnt) {
+    unsigned int* word = (unsigned int*)(tdead + (t & ~3));
+    unsigned int bit = 1u << (8 * (t & 3));
+    if (atomicOr(word, bit) & bit) return;          // the triangle died with another vertex
+    int32_t a = ta[t], b = tb[t], c = tc[t];
+    if (a != x) peel_drop(a, k, alive, deg, core, next, next_cnt);
+    if (b != x) peel_drop(b, k, alive, deg, core, next, next_cnt);
+    if (c != x) peel_drop(c, k, alive, deg, core, next, next_cnt);
+}
+
+// Whole peeling loop in one cooperative launch (peeling by levels).  A level k
+// starts with a scan of the live-vertex list: vertices with count <= k are
+// peeled (core k) into the frontier, the others go to the other list, and the
+// smallest kept count is recorded; an empty frontier moves k to
+// max(k + 1, that minimum) and scans again.  Frontier rounds then remove the
+// frontier and collect the vertices that fall to k.  One warp takes 32
+// frontier vertices: each lane removes its own if it has at most 32 incident
+// edges (triangles), and the warp removes the others together.  Once the live
+// list is down to `solo` vertices, block 0 finishes alone with block-wide
+// barriers, which cost far less than grid-wide ones over the many small
+// levels of the dense tail.
+// ctrl: [0..1] frontier counts, [2] smallest kept count, [3] error (bound hit),
+// [4..5] live-list counts.  Every thread follows the same k and the same
+// branches: the counters are read right after a barrier.
+__global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int64_t* rowptr, const int32_t* col,
+                                                         const int64_t* vptr, const int32_t* vtri, const int32_t* ta,
+                                                         const int32_t* tb, const int32_t* tc, uint8_t* tdead,
+                                                         uint8_t* alive, int32_t* deg, int64_t* core, int32_t* F0,
+                                                         int32_t* F1, int32_t* A0, int32_t* A1,
+                                                         unsigned long long* ctrl, int64_t max_steps, int64_t solo) {
     cg::grid_group grid = cg::this_grid();
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    int64_t k = 0;
-    for (int64_t step = 0;; ++step) {
-        if (step >= max_steps) {
+    bool whole = true;                       // all blocks take part (grid barriers)
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    auto barrier = [&]() {
+        if (whole) grid.sync();
+        else __syncthreads();
+    };
+    const int64_t* ptr = tri ? vptr : rowptr;
+    const int32_t* adj = tri ? vtri : col;
+    auto F = [&](int i) { return i ? F1 : F0; };
+    auto A = [&](int i) { return i ? A1 : A0; };
+    int cur = 0, a = 0;
+    int64_t k = 0, steps = 0;
+    for (;;) {
+        if (++steps > max_steps) {
             if (tid == 0) ctrl[3] = 1;
             return;
         }
-        for (int64_t x = tid; x < nact; x += nthreads) {
+        const int64_t na = (int64_t)__ldcg(ctrl + 4 + a);
+        if (whole && na <= solo) {
+            if (blockIdx.x != 0) return;
+            whole = false;
+            tid = threadIdx.x;
+            nthreads = blockDim.x;
+            warp = tid >> 5;
+            nwarps = nthreads >> 5;
+        }
+        // level scan
+        for (int64_t i = tid; i < na; i += nthreads) {
+            const int32_t x = __ldcg(A(a) + i);
             if (!__ldcg(alive + x)) continue;
-            int32_t d = __ldcg(deg + x);
+            const int32_t d = __ldcg(deg + x);
             if (d <= k) {
                 alive[x] = 0;
                 core[x] = k;
-                frontier[atomicAdd(ctrl, 1ull)] = (int32_t)x;
+                F(cur)[atomicAdd(ctrl + cur, 1ull)] = x;
             } else {
+                A(1 - a)[atomicAdd(ctrl + 5 - a, 1ull)] = x;
                 atomicMin(ctrl + 2, (unsigned long long)d);
             }
         }
-        grid.sync();
-        const unsigned long long f = __ldcg(ctrl);
-        const unsigned long long left = __ldcg(ctrl + 1);
+        barrier();
+        unsigned long long f = __ldcg(ctrl + cur);
+        const unsigned long long kept = __ldcg(ctrl + 5 - a);
         const unsigned long long mn = __ldcg(ctrl + 2);
-        grid.sync();
-        if (f == 0) {
-            if (left == 0) return;
-            k = max(k + 1, (int64_t)mn);
-            if (tid == 0) ctrl[2] = ~0ull;
-            grid.sync();
-            continue;
-        }
-        for (int64_t i = tid; i < (int64_t)f; i += nthreads) {
-            int32_t x = __ldcg(frontier + i);
-            if (!tri) {
-                for (int64_t s = rowptr[x], e = rowptr[x + 1]; s < e; ++s) {
-                    int32_t y = col[s];
-                    if (__ldcg(alive + y)) atomicSub(deg + y, 1);
-                }
-            } else {
-                for (int64_t s = vptr[x], e = vptr[x + 1]; s < e; ++s) {
-                    int32_t t = vtri[s];
-                    unsigned int* word = (unsigned int*)(tdead + (t & ~3));
-                    unsigned int bit = 1u << (8 * (t & 3));
-                    if (atomicOr(word, bit) & bit) continue;
-                    int32_t a = ta[t], b = tb[t], c = tc[t];
-                    if (a != x && __ldcg(alive + a)) atomicSub(deg + a, 1);
-                    if (b != x && __ldcg(alive + b)) atomicSub(deg + b, 1);
-                    if (c != x && __ldcg(alive + c)) atomicSub(deg + c, 1);
-                }
-            }
-        }
-        grid.sync();
+        barrier();
         if (tid == 0) {
-            ctrl[1] = left - f;
-            ctrl[0] = 0;
+            ctrl[4 + a] = 0;
             ctrl[2] = ~0ull;
         }
-        grid.sync();
-        if (left - f == 0) return;
+        a = 1 - a;
+        if (f == 0) {
+            if (kept == 0) return;
+            k = max(k + 1, (int64_t)mn);
+            barrier();
+            continue;
+        }
+        // frontier rounds at level k
+        while (f > 0) {
+            if (++steps > max_steps) {
+                if (tid == 0) ctrl[3] = 1;
+                return;
+            }
+            int32_t* fr = F(cur);
+            int32_t* nx = F(1 - cur);
+            unsigned long long* ncnt = ctrl + (1 - cur);
+            for (int64_t base = warp * 32; base < (int64_t)f; base += nwarps * 32) {
+                const int64_t i = base + lane;
+                int32_t x = -1;
+                int64_t b = 0, e = 0;
+                if (i < (int64_t)f) {
+                    x = __ldcg(fr + i);
+                    b = ptr[x];
+                    e = ptr[x + 1];
+                }
+                const bool heavy = e - b > 32;
+                if (!heavy)
+                    for (int64_t q = b; q < e; ++q) {
+                        if (tri) peel_triangle(adj[q], x, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
+                        else peel_drop(adj[q], k, alive, deg, core, nx, ncnt);
+                    }
+                unsigned hm = __ballot_sync(0xffffffffu, heavy);
+                while (hm) {
+                    const int src = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    const int32_t hx = __shfl_sync(0xffffffffu, x, src);
+                    const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
+                    for (int64_t q = hb + lane; q < he; q += 32) {
+                        if (tri) peel_triangle(adj[q], hx, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
+                        else peel_drop(adj[q], k, alive, deg, core, nx, ncnt);
+                    }
+                }
+            }
+            barrier();
+            f = __ldcg(ncnt);
+            barrier();
+            if (tid == 0) ctrl[cur] = 0;
+            cur = 1 - cur;
+            barrier();
+        }
+        k = k + 1;
     }
+}
+
+// list of the live vertices
+__global__ void alive_list_kernel(const uint8_t* alive, int32_t nact, int32_t* list, unsigned long long* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
+        if (alive[x]) list[atomicAdd(cnt, 1ull)] = (int32_t)x;
 }
 
 __global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
@@ -383,9 +426,8 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     const int32_t nact = g->nact;
     const int blk = 256;
     if (nact == 0) return;
-    DevBuf<int32_t> deg(nact, s), frontier(nact, s), fcount(1, s);
+    DevBuf<int32_t> deg(nact, s), frontier(nact, s);
     DevBuf<uint8_t> alive(nact, s);
-    DevBuf<int64_t> minalive(1, s);
     DevBuf<int32_t> nalive(1, s);
     LDS_CUDA(cudaMemsetAsync(nalive.get(), 0, sizeof(int32_t), s));
     LDS_LAUNCH(alive_init_kernel, grid_for(nact, blk), blk, 0, s, init_alive, nact, alive.get(), core_int, nalive.get());
@@ -408,16 +450,20 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_CUDA(cudaStreamSynchronize(s));
     if (remaining == 0) return;
     // one cooperative launch runs every level; the grid must be resident at once
-    DevBuf<unsigned long long> ctrl(4, s);
-    unsigned long long hctrl[4] = {0ull, (unsigned long long)remaining, ~0ull, 0ull};
+    DevBuf<unsigned long long> ctrl(6, s);
+    unsigned long long hctrl[6] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull};
     LDS_CUDA(cudaMemcpyAsync(ctrl.get(), hctrl, sizeof(hctrl), cudaMemcpyHostToDevice, s));
-    int dev = 0, per_sm = 0;
-    LDS_CUDA(cudaGetDevice(&dev));
-    LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_coop_kernel, blk, 0));
+    DevBuf<int32_t> F1(nact, s), A0(nact, s), A1(nact, s);
+    LDS_LAUNCH(alive_list_kernel, grid_for(nact, blk), blk, 0, s, alive.get(), nact, A0.get(), ctrl.get() + 4);
+    // one block of 1024 threads per SM: grid barriers get cheaper with fewer blocks
+    const int pblk = 1024;
+    int per_sm = 0;
+    LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_coop_kernel, pblk, 0));
     LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "core numbers: peeling kernel cannot be resident");
-    int grid = std::max(1, std::min(per_sm * num_sms(), (int)((nact + blk - 1) / blk)));
-    const int64_t max_steps = 4 * (int64_t)nact + 64;
-    const bool trib = tri;
+    int grid = std::max(1, std::min(num_sms(), (int)((nact + pblk - 1) / pblk)));
+    int64_t max_steps = 4 * (int64_t)nact + 64;
+    int64_t solo = 16384;
+    bool trib = tri;
     const int64_t* rp = g->rowptr.get();
     const int32_t* cl = g->col.get();
     const int64_t* vp = tri ? g->vt_ptr.get() : nullptr;
@@ -428,13 +474,15 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     uint8_t* td = tri ? tdead.get() : nullptr;
     uint8_t* al = alive.get();
     int32_t* dg = deg.get();
-    int32_t* fr = frontier.get();
+    int32_t* f0 = frontier.get();
+    int32_t* f1 = F1.get();
+    int32_t* a0 = A0.get();
+    int32_t* a1 = A1.get();
     unsigned long long* ct = ctrl.get();
-    int32_t nact_ = nact;
-    void* args[] = {&nact_, (void*)&trib, (void*)&rp, (void*)&cl, (void*)&vp, (void*)&vi, (void*)&pa, (void*)&pb,
-                    (void*)&pc, (void*)&td, (void*)&al, (void*)&dg, (void*)&core_int, (void*)&fr, (void*)&ct,
-                    (void*)&max_steps};
-    LDS_CUDA(cudaLaunchCooperativeKernel((void*)peel_coop_kernel, dim3(grid), dim3(blk), args, 0, s));
+    void* args[] = {(void*)&trib, (void*)&rp, (void*)&cl, (void*)&vp, (void*)&vi, (void*)&pa, (void*)&pb, (void*)&pc,
+                    (void*)&td, (void*)&al, (void*)&dg, (void*)&core_int, (void*)&f0, (void*)&f1, (void*)&a0,
+                    (void*)&a1, (void*)&ct, (void*)&max_steps, (void*)&solo};
+    LDS_CUDA(cudaLaunchCooperativeKernel((void*)peel_coop_kernel, dim3(grid), dim3(pblk), args, 0, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     LDS_CUDA(cudaMemcpyAsync(hctrl, ctrl.get(), sizeof(hctrl), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));

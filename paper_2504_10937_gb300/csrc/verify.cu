@@ -70,9 +70,12 @@ __global__ void edge_pat_count_kernel(const int32_t* list, int32_t k, int32_t na
     }
 }
 
+// share (optional): the Frank-Wolfe split of each edge, W = D alpha for its
+// lower endpoint x and D - W for y
 __global__ void edge_pat_fill_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
                                      const int32_t* col, const uint8_t* in, const int32_t* local, const int64_t* off,
-                                     int32_t* pidx) {
+                                     int32_t* pidx, const int64_t* slot_edge, const int64_t* W, int64_t D,
+                                     int64_t* share) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         int32_t x = list[i];
@@ -83,6 +86,11 @@ __global__ void edge_pat_fill_kernel(const int32_t* list, int32_t k, int32_t nac
                 if (y > x && in[y]) {
                     pidx[2 * o] = (int32_t)i;
                     pidx[2 * o + 1] = local[y];
+                    if (share) {
+                        const int64_t w = W[slot_edge[q]];
+                        share[2 * o] = w;
+                        share[2 * o + 1] = D - w;
+                    }
                     ++o;
                 }
             }
@@ -110,10 +118,14 @@ __global__ void uniform_pat_ptr_kernel(int64_t np, int64_t width, int64_t* pptr)
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= np; j += stride) pptr[j] = j * width;
 }
 
-__global__ void loop_fill_kernel(const int32_t* cnt, const int64_t* off, int32_t k, int32_t* pidx, int64_t base) {
+__global__ void loop_fill_kernel(const int32_t* cnt, const int64_t* off, int32_t k, int32_t* pidx, int64_t base,
+                                 int64_t* share) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride)
-        for (int32_t c = 0; c < cnt[i]; ++c) pidx[base + off[i] + c] = (int32_t)i;
+        for (int32_t c = 0; c < cnt[i]; ++c) {
+            pidx[base + off[i] + c] = (int32_t)i;
+            if (share) share[base + off[i] + c] = 1;
+        }
 }
 
 // triangles owned by their smallest member that is in the set (only those
@@ -124,7 +136,8 @@ __global__ void tri_pat_kernel(const int32_t* list, int32_t k, int32_t nact, con
                                const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
                                const uint8_t* in, const int32_t* local, bool all_in, const int64_t* un,
                                const int64_t* ud, const int64_t* ln, const int64_t* ld, int64_t p, int64_t q,
-                               int32_t* cnt, int32_t* len, const int64_t* off, int64_t* pptr, int32_t* pidx) {
+                               int32_t* cnt, int32_t* len, const int64_t* off, int64_t* pptr, int32_t* pidx,
+                               const int64_t* W, int64_t* share) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
         int32_t x = list[i];
@@ -142,7 +155,10 @@ __global__ void tri_pat_kernel(const int32_t* list, int32_t k, int32_t nact, con
                 if (all_in) {
                     if (!(in[v[0]] && in[v[1]] && in[v[2]])) continue;
                     if (FILL)
-                        for (int j = 0; j < 3; ++j) pidx[3 * o + j] = local[v[j]];
+                        for (int j = 0; j < 3; ++j) {
+                            pidx[3 * o + j] = local[v[j]];
+                            if (share) share[3 * o + j] = W[3 * (int64_t)t + j];
+                        }
                     ++c;
                     l += 3;
                     ++o;
@@ -160,7 +176,10 @@ __global__ void tri_pat_kernel(const int32_t* list, int32_t k, int32_t nact, con
                     if (FILL) {
                         int64_t at = pptr[o];
                         for (int j = 0; j < 3; ++j)
-                            if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) pidx[at++] = local[v[j]];
+                            if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) {
+                                if (share) share[at] = W[3 * (int64_t)t + j];
+                                pidx[at++] = local[v[j]];
+                            }
                     }
                     ++c;
                     l += mm;
@@ -390,11 +409,16 @@ static int64_t gcd64(int64_t a, int64_t b) {
 // Builds the pattern lists over `list` (k members, marked in sc.in with local
 // indices in sc.local).  Edge density: E(list) (+ loops when `loops` is set);
 // triangle density: T(list) when all_in, else Alg. 7's reduced patterns.
+// With `share`, it also receives the Frank-Wolfe split of every pattern
+// (aligned with pidx) when g holds Frank-Wolfe weights of the same density,
+// else it is released (the flow then splits evenly).
 static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch& sc, bool all_in,
                               bool loops, const Bounds* b, int64_t p, int64_t q, DevBuf<int64_t>& pptr,
-                              DevBuf<int32_t>& pidx, int64_t* n_main) {
+                              DevBuf<int32_t>& pidx, int64_t* n_main, DevBuf<int64_t>* share = nullptr) {
     cudaStream_t s = g->stream;
     const int32_t nact = g->nact;
+    const bool warm = share && g->fw_valid && g->fw_density == (tri ? LDS_TRIANGLE : LDS_EDGE);
+    if (share) share->release();
     DevBuf<int32_t> cnt(std::max(k, 1), s), len(std::max(k, 1), s);
     DevBuf<int64_t> off;
     if (!tri) {
@@ -412,6 +436,11 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
         const int64_t np = ne + nl;
         pptr.alloc(np + 1, s);
         pidx.alloc(std::max<int64_t>(2 * ne + nl, 1), s);
+        if (warm) {
+            ensure_slot_edge(g);
+            share->alloc(std::max<int64_t>(2 * ne + nl, 1), s);
+        }
+        int64_t* sh = warm ? share->get() : nullptr;
         // edge patterns first (width 2), then loops (width 1)
         LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(ne + 1, VB), VB, 0, s, ne, 2, pptr.get());
         if (nl) {
@@ -422,9 +451,10 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
         }
         if (k && ne)
             LDS_LAUNCH(edge_pat_fill_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
-                       sc.in.get(), sc.local.get(), off.get(), pidx.get());
+                       sc.in.get(), sc.local.get(), off.get(), pidx.get(), warm ? g->slot_edge.get() : nullptr,
+                       warm ? g->fw_W.get() : nullptr, g->fw_D, sh);
         if (k && nl)
-            LDS_LAUNCH(loop_fill_kernel, grid_for(k, VB), VB, 0, s, lcnt.get(), loff.get(), k, pidx.get(), 2 * ne);
+            LDS_LAUNCH(loop_fill_kernel, grid_for(k, VB), VB, 0, s, lcnt.get(), loff.get(), k, pidx.get(), 2 * ne, sh);
         if (n_main) *n_main = ne;
         return np;
     }
@@ -437,12 +467,15 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
     if (k)
         LDS_LAUNCH(tri_pat_kernel<false>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
                    g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
-                   cnt.get(), len.get(), (const int64_t*)nullptr, (int64_t*)nullptr, (int32_t*)nullptr);
+                   cnt.get(), len.get(), (const int64_t*)nullptr, (int64_t*)nullptr, (int32_t*)nullptr,
+                   (const int64_t*)nullptr, (int64_t*)nullptr);
     int64_t np = scan_counts(cnt.get(), k, off, s);
     DevBuf<int64_t> loffs;
     int64_t nidx = scan_counts(len.get(), k, loffs, s);
     pptr.alloc(np + 1, s);
     pidx.alloc(std::max<int64_t>(nidx, 1), s);
+    if (warm) share->alloc(std::max<int64_t>(nidx, 1), s);
+    int64_t* sh = warm ? share->get() : nullptr;
     if (all_in) {
         LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(np + 1, VB), VB, 0, s, np, 3, pptr.get());
     } else if (np) {
@@ -457,7 +490,8 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
     if (k && np)
         LDS_LAUNCH(tri_pat_kernel<true>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
                    g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
-                   (int32_t*)nullptr, (int32_t*)nullptr, off.get(), all_in ? (int64_t*)nullptr : pptr.get(), pidx.get());
+                   (int32_t*)nullptr, (int32_t*)nullptr, off.get(), all_in ? (int64_t*)nullptr : pptr.get(), pidx.get(),
+                   warm ? (const int64_t*)g->fw_W.get() : (const int64_t*)nullptr, sh);
     if (n_main) *n_main = np;
     return np;
 }
@@ -477,9 +511,9 @@ bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch&
     *npat = 0;
     if (k == 0) return false;
     LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), sc.local.get());
-    DevBuf<int64_t> pptr;
+    DevBuf<int64_t> pptr, share;
     DevBuf<int32_t> pidx;
-    int64_t np = build_patterns(g, tri, list, k, sc, true, false, nullptr, 0, 1, pptr, pidx, nullptr);
+    int64_t np = build_patterns(g, tri, list, k, sc, true, false, nullptr, 0, 1, pptr, pidx, nullptr, &share);
     *npat = np;
     bool ok = true;
     // a connected edge set with |E| = |S| - 1 is a tree: every proper subset has
@@ -488,7 +522,7 @@ bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch&
     if (np > 0 && !tree) {
         int64_t gg = gcd64(np, k);
         int64_t p = np / gg, q = k / gg;
-        int64_t f = pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, k, p, q, nullptr, s);
+        int64_t f = pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, k, p, q, share.get(), nullptr, true, s);
         ok = f == q * np;
     }
     LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
@@ -548,11 +582,11 @@ bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat
         // patterns over U: swap marks so that sc.in marks U with local indices
         LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
         LDS_LAUNCH(mark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get(), sc.local.get());
-        DevBuf<int64_t> pptr;
+        DevBuf<int64_t> pptr, share;
         DevBuf<int32_t> pidx;
-        int64_t np = build_patterns(g, tri, U.get(), usize, sc, false, !tri, &b, p, q, pptr, pidx, nullptr);
+        int64_t np = build_patterns(g, tri, U.get(), usize, sc, false, !tri, &b, p, q, pptr, pidx, nullptr, &share);
         DevBuf<uint8_t> side(usize, s);
-        pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, usize, p, q, side.get(), s);
+        pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, usize, p, q, share.get(), side.get(), false, s);
         if (st) ++st->flows;
         // A = source side; S must be a connected component of G[A]
         LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get());

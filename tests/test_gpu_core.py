@@ -192,6 +192,19 @@ def test_core_numbers(lds):
         assert np.array_equal(trcore, ograph.tr_core_numbers(n, ograph.triangles(n, u, v)))
 
 
+def test_core_numbers_large(lds):
+    # more live vertices than the single-block tail takes, so the grid-wide
+    # levels and the hand-over to one block both run
+    n, u, v, _ = synth.chung_lu(40000, 400000, 2.1, seed=5, n_blocks=4, block_size_range=(50, 120))
+    with lds.Graph(n, u, v) as g:
+        core = g.core_numbers("edge")
+    assert np.array_equal(core, ograph.core_numbers(n, u, v))
+    n, u, v, _ = synth.chung_lu(20000, 120000, 2.1, seed=6, n_blocks=3, block_size_range=(30, 60))
+    with lds.Graph(n, u, v) as g:
+        trcore = g.core_numbers("triangle")
+    assert np.array_equal(trcore, ograph.tr_core_numbers(n, ograph.triangles(n, u, v)))
+
+
 def test_injected_allocation_failure_reports_enomem(lds):
     n, u, v = _graphs()[1]
     lds.debug_fail_alloc_after(3)
