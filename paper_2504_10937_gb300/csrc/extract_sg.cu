@@ -186,20 +186,15 @@ __global__ void seg_of_pos_kernel(const int64_t* sa, const int64_t* sb, int32_t 
     }
 }
 
+// Records are written in two passes: the first stores the number of records
+// of every position (cnt), the second writes them from that position's offset
+// (off, the exclusive scan of cnt), so no counter is shared.
 struct Rec {
     uint64_t* key;
     int64_t* val;
-    unsigned long long* count;
-    int64_t cap;
+    int64_t* cnt;          // [positions] count pass
+    const int64_t* off;    // [positions] fill pass
 };
-
-__device__ __forceinline__ void push_rec(const Rec& r, uint64_t key, int64_t val) {
-    unsigned long long i = atomicAdd(r.count, 1ull);
-    if ((int64_t)i < r.cap) {
-        r.key[i] = key;
-        r.val[i] = val;
-    }
-}
 
 // edge check, one thread per position of a checked segment
 __global__ void check_edges_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof, const int64_t* sa,
@@ -213,25 +208,31 @@ __global__ void check_edges_kernel(const int32_t* order, const int32_t* pos, con
         int32_t x = order[p];
         if (x < nact) {                              // isolated vertices have no row
             int64_t a = sa[s], b = sb[s];
-            int64_t d = 0;
+            int64_t d = 0, c = 0;
+            int64_t o = count_only ? 0 : rec.off[p - npos_lo];
             for (int64_t q = rowptr[x], e = rowptr[x + 1]; q < e; ++q) {
                 int32_t y = col[q];
                 int64_t py = pos[y];
                 if (py >= a && py <= b) continue;
+                if (count_only) {
+                    ++c;
+                    continue;
+                }
                 int64_t ed = slot_edge[q];
                 int64_t share_x = (eu[ed] == x) ? W[ed] : Dn - W[ed];
                 int64_t share_y = Dn - share_x;
-                if (count_only) {
-                    atomicAdd(rec.count, 1ull);
-                } else if (py < a) {                 // y in X: the edge goes to x
+                rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)y;
+                if (py < a) {                        // y in X: the edge goes to x
                     d += share_y;
-                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)y, -share_y);
+                    rec.val[o] = -share_y;
                 } else {                             // y in Z: the edge goes to y
                     d -= share_x;
-                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)y, share_x);
+                    rec.val[o] = share_x;
                 }
+                ++o;
             }
-            if (!count_only) deltaS[p - npos_lo] = d;
+            if (count_only) rec.cnt[p - npos_lo] = c;
+            else deltaS[p - npos_lo] = d;
         }
     }
 }
@@ -250,6 +251,8 @@ __global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, cons
         int32_t x = order[p];
         if (x >= nact) continue;                     // isolated vertices lie in no triangle
         int64_t a = sa[s], b = sb[s];
+        int64_t c = 0;
+        int64_t o = count_only ? 0 : rec.off[p - npos_lo];
         for (int64_t q = vt_ptr[x], e = vt_ptr[x + 1]; q < e; ++q) {
             int32_t t = vt_idx[q];
             int32_t v[3] = {ta[t], tb[t], tc[t]};
@@ -279,19 +282,22 @@ __global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, cons
                 if (pp[k] >= a && pp[k] <= b) {
                     if (!count_only) atomicAdd(deltaS + (pp[k] - npos_lo), (unsigned long long)(-w));
                 } else if (count_only) {
-                    atomicAdd(rec.count, 1ull);
+                    ++c;
                 } else {
-                    push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)v[k], -w);
+                    rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[k];
+                    rec.val[o++] = -w;
                 }
             }
             if (pp[tgt] >= a && pp[tgt] <= b) {
                 if (!count_only) atomicAdd(deltaS + (pp[tgt] - npos_lo), (unsigned long long)moved);
             } else if (count_only) {
-                atomicAdd(rec.count, 1ull);
+                ++c;
             } else {
-                push_rec(rec, (uint64_t)s * (uint64_t)n + (uint64_t)v[tgt], moved);
+                rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[tgt];
+                rec.val[o++] = moved;
             }
         }
+        if (count_only) rec.cnt[p - npos_lo] = c;
     }
 }
 
@@ -420,25 +426,22 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
     LDS_LAUNCH(seg_of_pos_kernel, grid_for(phi - plo, blk), blk, 0, s, sa.get(), sb.get(), nseg, plo, phi, segof);
     DevBuf<int64_t> deltaS(phi - plo, s);
     LDS_CUDA(cudaMemsetAsync(deltaS.get(), 0, (phi - plo) * sizeof(int64_t), s));
-    DevBuf<unsigned long long> rcnt(1, s);
     const int64_t* W = g->fw_W.get();
     const int32_t nact = g->nact;
-    // two passes: count the records, then fill an exactly sized buffer
+    // two passes: count the records of every position, then fill an exactly sized buffer
     DevBuf<uint64_t> rkey;
     DevBuf<int64_t> rval;
+    DevBuf<int64_t> rcnt(phi - plo, s), roff(phi - plo, s);
+    LDS_CUDA(cudaMemsetAsync(rcnt.get(), 0, (phi - plo) * sizeof(int64_t), s));
+    int64_t nrec = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const bool count_only = pass == 0;
-        int64_t cap = 0;
         if (!count_only) {
-            unsigned long long c = 0;
-            LDS_CUDA(cudaMemcpyAsync(&c, rcnt.get(), sizeof(c), cudaMemcpyDeviceToHost, s));
-            LDS_CUDA(cudaStreamSynchronize(s));
-            cap = (int64_t)c;
-            rkey.alloc(std::max<int64_t>(cap, 1), s);
-            rval.alloc(std::max<int64_t>(cap, 1), s);
+            nrec = exclusive_scan_i64(rcnt.get(), roff.get(), phi - plo, s);
+            rkey.alloc(std::max<int64_t>(nrec, 1), s);
+            rval.alloc(std::max<int64_t>(nrec, 1), s);
         }
-        LDS_CUDA(cudaMemsetAsync(rcnt.get(), 0, sizeof(unsigned long long), s));
-        Rec rec{rkey.get(), rval.get(), rcnt.get(), cap};
+        Rec rec{rkey.get(), rval.get(), rcnt.get(), roff.get()};
         if (!tri) {
             if (g->m) {
                 ensure_slot_edge(g);
@@ -453,11 +456,6 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
                        g->tc.get(), W, n, nact, (unsigned long long*)deltaS.get(), rec, count_only);
         }
     }
-    const int64_t cap = (int64_t)rkey.n;
-    unsigned long long nrec = 0;
-    LDS_CUDA(cudaMemcpyAsync(&nrec, rcnt.get(), sizeof(nrec), cudaMemcpyDeviceToHost, s));
-    LDS_CUDA(cudaStreamSynchronize(s));
-    LDS_REQUIRE((int64_t)nrec <= cap, LDS_ECUDA, "extract_sg: record buffer overflow (internal error)");
     DevBuf<long long> dminS(nseg, s), dmaxS(nseg, s), dminX(nseg, s), dmaxZ(nseg, s);
     LDS_LAUNCH(side_init_kernel, grid_for(nseg, blk), blk, 0, s, sa.get(), sb.get(), nseg, n, st.order.get(),
                g->fw_R.get(), dminS.get(), dmaxS.get(), dminX.get(), dmaxZ.get());

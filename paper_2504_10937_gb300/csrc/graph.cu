@@ -65,6 +65,7 @@ __global__ void nonisolated_flag_kernel(const int32_t* deg, int32_t n, int32_t* 
 __global__ void id_maps_kernel(const int32_t* deg, const int64_t* nz_rank, int32_t n, int32_t nact,
                                int32_t* to_int, int32_t* to_orig, int32_t* deg_int, int* maxdeg) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int32_t dmax = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         int32_t d = deg[i];
         int32_t id = d > 0 ? (int32_t)nz_rank[i] : (int32_t)(nact + (i - nz_rank[i]));
@@ -72,9 +73,10 @@ __global__ void id_maps_kernel(const int32_t* deg, const int64_t* nz_rank, int32
         to_orig[id] = (int32_t)i;
         if (d > 0) {
             deg_int[id] = d;
-            atomicMax(maxdeg, d);
+            dmax = max(dmax, d);
         }
     }
+    if (dmax) atomicMax(maxdeg, dmax);
 }
 
 __global__ void fill_csr_kernel(const uint64_t* ukeys, int64_t k2, int64_t n, const int32_t* to_int,

@@ -76,17 +76,25 @@ __global__ void apply_groups_kernel(const int32_t* order, const int64_t* gend, c
 // group id of every position (accepted groups 0..ng-1, remainder ng) and kept flag
 __global__ void group_keys_kernel(const int32_t* order, const int64_t* gend, int32_t ng, int32_t n, const uint8_t* status,
                                   int32_t* gid, int32_t* keep, int32_t* gcount) {
+    // warp-uniform loop; lanes of one group add their count with one atomic
+    const int lane = threadIdx.x & 31;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        int lo_i = 0, hi_i = ng;
-        while (lo_i < hi_i) {
-            int mid = (lo_i + hi_i) >> 1;
-            if (gend[mid] > p) hi_i = mid; else lo_i = mid + 1;
+    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; p0 < n; p0 += stride) {
+        const int64_t p = p0 + lane;
+        int key = -1;
+        if (p < n) {
+            int lo_i = 0, hi_i = ng;
+            while (lo_i < hi_i) {
+                int mid = (lo_i + hi_i) >> 1;
+                if (gend[mid] > p) hi_i = mid; else lo_i = mid + 1;
+            }
+            int32_t k = status[order[p]] == 0;
+            gid[p] = lo_i;
+            keep[p] = k;
+            if (k) key = lo_i;
         }
-        int32_t k = status[order[p]] == 0;
-        gid[p] = lo_i;
-        keep[p] = k;
-        if (k) atomicAdd(gcount + lo_i, 1);
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(gcount + key, __popc(peers));
     }
 }
 

@@ -15,6 +15,8 @@
 #include <algorithm>
 
 #include <cooperative_groups.h>
+#include <cstdio>
+#include <cstdlib>
 
 #include "graph.cuh"
 #include "prims.cuh"
@@ -196,17 +198,26 @@ __global__ void alive_tri_count_kernel(const int32_t* ta, const int32_t* tb, con
     }
 }
 
-// Removes one peeled vertex x at level k: every live neighbour (edge) or
-// every other vertex of each live triangle of x loses one; a vertex whose
-// count falls from k + 1 to k is peeled at level k too (exactly one decrement
-// sees k + 1) and joins the next frontier.
+// one atomic per group of converged threads that append together
+__device__ __forceinline__ unsigned long long agg_slot(unsigned long long* ctr) {
+    cg::coalesced_group grp = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (grp.thread_rank() == 0) base = atomicAdd(ctr, (unsigned long long)grp.size());
+    return grp.shfl(base, 0) + grp.thread_rank();
+}
+
+// Removing a peeled vertex at level k lowers the count of each neighbour (of
+// each other vertex of each live triangle); a vertex whose count falls from
+// k + 1 to k is peeled at level k too (exactly one decrement sees k + 1) and
+// joins the next frontier.  Counts of vertices already peeled are lowered as
+// well: theirs are at most their level <= k and only fall, so they never see
+// k + 1 again, and skipping a liveness test saves a dependent load.
 __device__ __forceinline__ void peel_drop(int32_t y, int64_t k, uint8_t* alive, int32_t* deg, int64_t* core,
                                           int32_t* next, unsigned long long* next_cnt) {
-    if (!__ldcg(alive + y)) return;
     if ((int64_t)atomicSub(deg + y, 1) == k + 1) {
         alive[y] = 0;
         core[y] = k;
-        next[atomicAdd(next_cnt, 1ull)] = y;
+        next[agg_slot(next_cnt)] = y;
     }
 }
 
@@ -222,26 +233,32 @@ __device__ __forceinline__ void peel_triangle(int32_t t, int32_t x, int64_t k, c
     if (c != x) peel_drop(c, k, alive, deg, core, next, next_cnt);
 }
 
+constexpr int PEEL_LIGHT = 8;       // a lane removes a vertex with at most this many incidences
+constexpr int PEEL_CHUNK = 128;     // otherwise a warp removes each chunk of this many (4 per lane)
+
 // Whole peeling loop in one cooperative launch (peeling by levels).  A level k
 // starts with a scan of the live-vertex list: vertices with count <= k are
 // peeled (core k) into the frontier, the others go to the other list, and the
 // smallest kept count is recorded; an empty frontier moves k to
 // max(k + 1, that minimum) and scans again.  Frontier rounds then remove the
-// frontier and collect the vertices that fall to k.  One warp takes 32
-// frontier vertices: each lane removes its own if it has at most 32 incident
-// edges (triangles), and the warp removes the others together.  Once the live
-// list is down to `solo` vertices, block 0 finishes alone with block-wide
-// barriers, which cost far less than grid-wide ones over the many small
-// levels of the dense tail.
+// frontier and collect the vertices that fall to k: a lane removes a vertex
+// with few incidences itself, and the incidences of the others are cut into
+// chunks that all warps share, so a hub does not hold up the round.  Once the
+// live list is down to `solo` vertices, block 0 finishes alone with
+// block-wide barriers, which cost far less than grid-wide ones over the many
+// small levels of the dense tail.
 // ctrl: [0..1] frontier counts, [2] smallest kept count, [3] error (bound hit),
-// [4..5] live-list counts.  Every thread follows the same k and the same
-// branches: the counters are read right after a barrier.
+// [4..5] live-list counts, [6..7] steps and last level (reported at the end),
+// [8] chunk count.  Every thread follows the same k and the same branches: the
+// counters are read right after a barrier.
 __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int64_t* rowptr, const int32_t* col,
-                                                         const int64_t* vptr, const int32_t* vtri, const int32_t* ta,
-                                                         const int32_t* tb, const int32_t* tc, uint8_t* tdead,
-                                                         uint8_t* alive, int32_t* deg, int64_t* core, int32_t* F0,
-                                                         int32_t* F1, int32_t* A0, int32_t* A1,
-                                                         unsigned long long* ctrl, int64_t max_steps, int64_t solo) {
+                                                            const int64_t* vptr, const int32_t* vtri,
+                                                            const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                                            uint8_t* tdead, uint8_t* alive, int32_t* deg,
+                                                            int64_t* core, int32_t* F0, int32_t* F1, int32_t* A0,
+                                                            int32_t* A1, int32_t* qv, int64_t* qs,
+                                                            unsigned long long* ctrl, int64_t max_steps,
+                                                            int64_t solo) {
     cg::grid_group grid = cg::this_grid();
     bool whole = true;                       // all blocks take part (grid barriers)
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,19 +289,38 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
             warp = tid >> 5;
             nwarps = nthreads >> 5;
         }
-        // level scan
-        for (int64_t i = tid; i < na; i += nthreads) {
-            const int32_t x = __ldcg(A(a) + i);
-            if (!__ldcg(alive + x)) continue;
-            const int32_t d = __ldcg(deg + x);
-            if (d <= k) {
+        // level scan, warp by warp: one atomic per warp for each list and for the minimum
+        for (int64_t base = tid - lane; base < na; base += nthreads) {
+            const int64_t i = base + lane;
+            int32_t x = -1, d = 0;
+            bool peel = false, keep = false;
+            if (i < na) {
+                x = __ldcg(A(a) + i);
+                if (__ldcg(alive + x)) {
+                    d = __ldcg(deg + x);
+                    peel = d <= k;
+                    keep = !peel;
+                }
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, peel), km = __ballot_sync(0xffffffffu, keep);
+            const unsigned dmin = __reduce_min_sync(0xffffffffu, keep ? (unsigned)d : 0xffffffffu);
+            unsigned long long pb = 0, kb = 0;
+            if (lane == 0) {
+                if (pm) pb = atomicAdd(ctrl + cur, (unsigned long long)__popc(pm));
+                if (km) {
+                    kb = atomicAdd(ctrl + 5 - a, (unsigned long long)__popc(km));
+                    atomicMin(ctrl + 2, (unsigned long long)dmin);
+                }
+            }
+            pb = __shfl_sync(0xffffffffu, pb, 0);
+            kb = __shfl_sync(0xffffffffu, kb, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (peel) {
                 alive[x] = 0;
                 core[x] = k;
-                F(cur)[atomicAdd(ctrl + cur, 1ull)] = x;
-            } else {
-                A(1 - a)[atomicAdd(ctrl + 5 - a, 1ull)] = x;
-                atomicMin(ctrl + 2, (unsigned long long)d);
+                F(cur)[pb + __popc(pm & below)] = x;
             }
+            if (keep) A(1 - a)[kb + __popc(km & below)] = x;
         }
         barrier();
         unsigned long long f = __ldcg(ctrl + cur);
@@ -297,7 +333,13 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         }
         a = 1 - a;
         if (f == 0) {
-            if (kept == 0) return;
+            if (kept == 0) {
+                if (tid == 0) {
+                    ctrl[6] = (unsigned long long)steps;
+                    ctrl[7] = (unsigned long long)k;
+                }
+                return;
+            }
             k = max(k + 1, (int64_t)mn);
             barrier();
             continue;
@@ -311,37 +353,70 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
             int32_t* fr = F(cur);
             int32_t* nx = F(1 - cur);
             unsigned long long* ncnt = ctrl + (1 - cur);
+            // light vertices by their lane; chunks of the heavy ones into the queue
             for (int64_t base = warp * 32; base < (int64_t)f; base += nwarps * 32) {
                 const int64_t i = base + lane;
                 int32_t x = -1;
-                int64_t b = 0, e = 0;
+                int64_t b = 0, len = 0;
                 if (i < (int64_t)f) {
                     x = __ldcg(fr + i);
                     b = ptr[x];
-                    e = ptr[x + 1];
+                    len = ptr[x + 1] - b;
                 }
-                const bool heavy = e - b > 32;
-                if (!heavy)
-                    for (int64_t q = b; q < e; ++q) {
-                        if (tri) peel_triangle(adj[q], x, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
-                        else peel_drop(adj[q], k, alive, deg, core, nx, ncnt);
-                    }
-                unsigned hm = __ballot_sync(0xffffffffu, heavy);
-                while (hm) {
-                    const int src = __ffs(hm) - 1;
-                    hm &= hm - 1;
-                    const int32_t hx = __shfl_sync(0xffffffffu, x, src);
-                    const int64_t hb = __shfl_sync(0xffffffffu, b, src), he = __shfl_sync(0xffffffffu, e, src);
-                    for (int64_t q = hb + lane; q < he; q += 32) {
-                        if (tri) peel_triangle(adj[q], hx, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
-                        else peel_drop(adj[q], k, alive, deg, core, nx, ncnt);
-                    }
+                if (len <= PEEL_LIGHT) {
+                    int32_t it[PEEL_LIGHT];
+#pragma unroll
+                    for (int j = 0; j < PEEL_LIGHT; ++j) it[j] = j < len ? adj[b + j] : -1;
+#pragma unroll
+                    for (int j = 0; j < PEEL_LIGHT; ++j)
+                        if (it[j] >= 0) {
+                            if (tri) peel_triangle(it[j], x, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
+                            else peel_drop(it[j], k, alive, deg, core, nx, ncnt);
+                        }
                 }
+                const int32_t nch = len > PEEL_LIGHT ? (int32_t)((len + PEEL_CHUNK - 1) / PEEL_CHUNK) : 0;
+                int32_t incl = nch;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                const int32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+                unsigned long long cb = 0;
+                if (lane == 0 && tot) cb = atomicAdd(ctrl + 8, (unsigned long long)tot);
+                cb = __shfl_sync(0xffffffffu, cb, 0);
+                for (int32_t c = 0; c < nch; ++c) {
+                    const unsigned long long at = cb + (unsigned long long)(incl - nch + c);
+                    qv[at] = x;
+                    qs[at] = b + (int64_t)c * PEEL_CHUNK;
+                }
+            }
+            barrier();
+            const int64_t nq = (int64_t)__ldcg(ctrl + 8);
+            for (int64_t c = warp; c < nq; c += nwarps) {
+                const int32_t x = __ldcg(qv + c);
+                const int64_t q0 = __ldcg(qs + c);
+                const int64_t q1 = min(q0 + (int64_t)PEEL_CHUNK, ptr[x + 1]);
+                int32_t it[PEEL_CHUNK / 32];
+#pragma unroll
+                for (int j = 0; j < PEEL_CHUNK / 32; ++j) {
+                    const int64_t q = q0 + lane + 32 * j;
+                    it[j] = q < q1 ? adj[q] : -1;
+                }
+#pragma unroll
+                for (int j = 0; j < PEEL_CHUNK / 32; ++j)
+                    if (it[j] >= 0) {
+                        if (tri) peel_triangle(it[j], x, k, ta, tb, tc, tdead, alive, deg, core, nx, ncnt);
+                        else peel_drop(it[j], k, alive, deg, core, nx, ncnt);
+                    }
             }
             barrier();
             f = __ldcg(ncnt);
             barrier();
-            if (tid == 0) ctrl[cur] = 0;
+            if (tid == 0) {
+                ctrl[cur] = 0;
+                ctrl[8] = 0;
+            }
             cur = 1 - cur;
             barrier();
         }
@@ -353,7 +428,7 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
 __global__ void alive_list_kernel(const uint8_t* alive, int32_t nact, int32_t* list, unsigned long long* cnt) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
-        if (alive[x]) list[atomicAdd(cnt, 1ull)] = (int32_t)x;
+        if (alive[x]) list[agg_slot(cnt)] = (int32_t)x;
 }
 
 __global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
@@ -450,10 +525,15 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_CUDA(cudaStreamSynchronize(s));
     if (remaining == 0) return;
     // one cooperative launch runs every level; the grid must be resident at once
-    DevBuf<unsigned long long> ctrl(6, s);
-    unsigned long long hctrl[6] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull};
+    DevBuf<unsigned long long> ctrl(9, s);
+    unsigned long long hctrl[9] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     LDS_CUDA(cudaMemcpyAsync(ctrl.get(), hctrl, sizeof(hctrl), cudaMemcpyHostToDevice, s));
     DevBuf<int32_t> F1(nact, s), A0(nact, s), A1(nact, s);
+    // chunk queue: at most one chunk per vertex plus one per PEEL_CHUNK incidences
+    const int64_t incid = tri ? 3 * g->ntri : 2 * g->m;
+    const int64_t qcap = (int64_t)nact + incid / PEEL_CHUNK + 1;
+    DevBuf<int32_t> qv(qcap, s);
+    DevBuf<int64_t> qs(qcap, s);
     LDS_LAUNCH(alive_list_kernel, grid_for(nact, blk), blk, 0, s, alive.get(), nact, A0.get(), ctrl.get() + 4);
     // one block of 1024 threads per SM: grid barriers get cheaper with fewer blocks
     const int pblk = 1024;
@@ -479,13 +559,32 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     int32_t* a0 = A0.get();
     int32_t* a1 = A1.get();
     unsigned long long* ct = ctrl.get();
+    int32_t* qvp = qv.get();
+    int64_t* qsp = qs.get();
     void* args[] = {(void*)&trib, (void*)&rp, (void*)&cl, (void*)&vp, (void*)&vi, (void*)&pa, (void*)&pb, (void*)&pc,
                     (void*)&td, (void*)&al, (void*)&dg, (void*)&core_int, (void*)&f0, (void*)&f1, (void*)&a0,
-                    (void*)&a1, (void*)&ct, (void*)&max_steps, (void*)&solo};
+                    (void*)&a1, (void*)&qvp, (void*)&qsp, (void*)&ct, (void*)&max_steps, (void*)&solo};
+    const char* vb = getenv("LDS_VERBOSE");
+    const bool verbose = vb && vb[0] == '1';
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (verbose) {
+        LDS_CUDA(cudaEventCreate(&e0));
+        LDS_CUDA(cudaEventCreate(&e1));
+        LDS_CUDA(cudaEventRecord(e0, s));
+    }
     LDS_CUDA(cudaLaunchCooperativeKernel((void*)peel_coop_kernel, dim3(grid), dim3(pblk), args, 0, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (verbose) LDS_CUDA(cudaEventRecord(e1, s));
     LDS_CUDA(cudaMemcpyAsync(hctrl, ctrl.get(), sizeof(hctrl), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
+    if (verbose) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        fprintf(stderr, "[core] nact=%d live=%d peel %.2f ms, %llu steps, last level %llu, grid %d\n", nact, remaining,
+                ms, hctrl[6], hctrl[7], grid);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     LDS_REQUIRE(hctrl[3] == 0, LDS_ETIMEOUT, "core numbers: peeling hit its iteration bound");
 }
 
