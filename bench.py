@@ -39,6 +39,11 @@ from paper_2504_10937_gb300 import synth  # noqa: E402
 METRIC = "FW edge-updates/s"
 UNIT = "edge-updates/s"
 
+# DRAM bytes (read + write) of one launch of the pass kernel on this workload, from
+# one ncu capture of the current kernel (see profiles/); a kernel changed since
+# then has no entry and reports null.
+PASS_TRAFFIC = {}
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -298,10 +303,17 @@ def run_ours(args):
                  "ms_per_query": 1000.0 * statistics.mean(pt)}
 
     hbm, peak_kind = _peaks()
-    bytes_per_pass = last_timing["pass_bytes"]
+    # algorithmic bytes of one pass: 16 B per edge in EXACT and FP32 (8 B of ids, 8 B of
+    # alpha read-modify-write), 24 B in FP64; the kernel itself moves fewer (kernel_bytes)
+    per_edge = {"exact": 16, "fp32": 16, "fp64": 24}[args.precision]
+    bytes_per_pass = per_edge * m
     avg_pass_us = statistics.mean(pass_us)
     achieved = bytes_per_pass / (avg_pass_us * 1e-6) / 1e9
     clocks = clk.summary()
+    lat = sorted(times)
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,14 +324,18 @@ def run_ours(args):
             "fw_only": {"value": m * args.iters / (statistics.mean(fw_ms) / 1000.0), "unit": UNIT,
                         "fw_ms": statistics.mean(fw_ms), "note": "first-round FW kernels on G only"},
             "queries_per_s": None if args.fw_only else 1000.0 * args.steps / total_ms,
+            "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "n": len(lat)},
             "plain_fp64_gpu": plain,
             "phases_ms": None if args.fw_only else {k: statistics.mean(p[k] for p in phase)
                                                      for k in ("ms_total", "ms_fw", "ms_extract", "ms_prune",
                                                                "ms_verify")},
             "result": None if args.fw_only else [[str(d), len(c)] for d, c in m_holder["result"]],
             "roofline": {"bound": "hbm", "kernel": last_timing["pass_kernel"], "achieved": achieved, "peak": hbm,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                         "algorithmic_bytes_per_launch": bytes_per_pass, "avg_launch_us": avg_pass_us},
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": PASS_TRAFFIC.get((last_timing["pass_kernel"], args.precision)),
+                         "algorithmic_bytes_per_launch": bytes_per_pass, "bytes_per_edge": per_edge,
+                         "kernel_bytes_per_launch": last_timing["pass_bytes"], "avg_launch_us": avg_pass_us,
+                         "launches_timed": len(pass_us)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * len(a)),
                     "d2h_bytes_per_step": int(8 * n)},
             "gpu_launches": int(launches),

@@ -557,8 +557,26 @@ void extract_sg(lds_graph* g, SgState& st) {
     }
     DevBuf<int32_t> segof(n, s);
     LDS_LAUNCH(fill_i32_range_kernel, grid_for(n, blk), blk, 0, s, segof.get(), 0, n, -1);
-    std::vector<long long> mnS, mxS, mnX, mxZ;
-    check_segments(g, st, segof.get(), ca, cb, mnS, mxS, mnX, mxZ);
+    // Single-candidate checks are independent of one another; they are run
+    // lazily, in batches of growing size, because the walk below often stops
+    // long before the last candidate.
+    const size_t ncand = ca.size();
+    std::vector<long long> mnS(ncand), mxS(ncand), mnX(ncand), mxZ(ncand);
+    size_t checked = 0, batch = 256;
+    auto ensure_checked = [&](size_t k) {
+        while (checked <= k) {
+            const size_t hi = std::min(ncand, checked + batch);
+            std::vector<int64_t> a(ca.begin() + checked, ca.begin() + hi), b(cb.begin() + checked, cb.begin() + hi);
+            std::vector<long long> r1, r2, r3, r4;
+            check_segments(g, st, segof.get(), a, b, r1, r2, r3, r4);
+            std::copy(r1.begin(), r1.end(), mnS.begin() + checked);
+            std::copy(r2.begin(), r2.end(), mxS.begin() + checked);
+            std::copy(r3.begin(), r3.end(), mnX.begin() + checked);
+            std::copy(r4.begin(), r4.end(), mxZ.begin() + checked);
+            checked = hi;
+            batch = std::min<size_t>(batch * 4, (size_t)1 << 22);
+        }
+    };
     // For a fixed start, growing the segment only lowers the X vertices' modified
     // loads and only raises max_S r': once the X-side test fails it fails for
     // every longer merge, so the whole rest is the unaccepted remainder.
@@ -566,6 +584,7 @@ void extract_sg(lds_graph* g, SgState& st) {
     for (size_t k = 0; k < ca.size(); ++k) {
         long long lo, hi, mx, mz;
         if (ca[k] == start) {
+            ensure_checked(k);
             lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
             std::vector<int64_t> a1{start}, b1{cb[k]};
