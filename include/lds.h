@@ -236,6 +236,75 @@ void lds_result_free(lds_result* r);
 
 lds_status lds_topk_last_stats(lds_topk_stats_t* stats);
 
+/* ---- Many queries at once: batches and the serving loop.
+ * Neither has a counterpart in the paper, which defines one query at a time;
+ * both run the queries of lds_topk unchanged (same kernels, same answers) and
+ * only decide when each one runs.  Worker threads, each with its own
+ * non-blocking CUDA stream, take queries from a FIFO queue; a query starts
+ * when its graph handle is idle (queries on one handle run one after another)
+ * and its estimated device footprint fits in what is left of the memory
+ * budget; among those the oldest starts first.  Queries on different handles
+ * overlap on the device.  While a query runs, its handle works on the
+ * worker's stream; the handle's own stream is synchronised before and given
+ * back after.  The caller must not use a handle while one of its queries is
+ * queued or running. */
+typedef struct {
+    lds_graph*    g;        /* graph handle (owned by the caller)          */
+    int32_t       k;        /* number of sets wanted (>= 1)                 */
+    lds_density   d;        /* LDS_EDGE (LDS) or LDS_TRIANGLE (LTDS)        */
+    int32_t       iters;    /* Frank-Wolfe iterations per round (>= 1)      */
+    lds_precision p;        /* arithmetic of the iterations                 */
+} lds_query;
+
+typedef struct lds_server lds_server;
+
+/* Per-request timing of the serving loop. */
+typedef struct {
+    double  queue_ms;          /* submit -> start                             */
+    double  run_ms;            /* start -> end                                */
+    int64_t footprint_bytes;   /* the estimate the admission used             */
+    lds_topk_stats_t stats;    /* the query's counters                        */
+} lds_request_info;
+
+/* Starts `workers` worker threads on the current device with a device-memory
+ * budget of `budget_bytes` for the queries in flight.  A query's footprint is
+ * estimated as 96 B per edge and per vertex plus 64 B per triangle for LTDS
+ * (16 per edge stands in for |T| while the triangles are not listed yet).
+ * Errors: LDS_EINVAL, LDS_ECUDA. */
+lds_status lds_server_create(int64_t budget_bytes, int32_t workers, lds_server** out);
+
+/* Queues one query and returns its ticket at once.  LDS_EBUSY when the query's
+ * footprint alone exceeds the budget; LDS_EINVAL on a bad query. */
+lds_status lds_server_submit(lds_server* s, const lds_query* q, int64_t* ticket);
+
+/* *done = 1 once the query has finished (successfully or not). */
+lds_status lds_server_poll(lds_server* s, int64_t ticket, int32_t* done);
+
+/* Blocks until the query has finished, then hands over its result (free with
+ * lds_result_free) and, if info is not NULL, its timing.  Returns the query's
+ * own status; the ticket is retired either way. */
+lds_status lds_server_wait(lds_server* s, int64_t ticket, lds_result** out, lds_request_info* info);
+
+/* Runs every queued query to the end, stops the workers and frees what was
+ * not collected. */
+void lds_server_destroy(lds_server* s);
+
+/* Runs `count` queries with `workers` worker threads (0: the count chosen by
+ * lds_batch_autotune) and no memory budget.  results[i] / status[i] belong to
+ * queries[i]; the return value is the first failure, or LDS_OK. */
+lds_status lds_topk_batch(int32_t count, const lds_query* queries, int32_t workers, lds_result** results,
+                          lds_status* status);
+
+/* Worker count for a batch: times the first min(count, 64) queries with 1, 2,
+ * 4, 8 and 16 workers and keeps the fastest; the choice is cached per size
+ * bucket (log2 of the mean edge count) for the rest of the process. */
+lds_status lds_batch_autotune(int32_t count, const lds_query* queries, int32_t* workers);
+
+/* The admission rule itself, for tests: index of the request the serving loop
+ * would start next among nq queued ones (oldest first) given their footprints,
+ * whether each one's graph is busy, and the free budget; -1 if none fits. */
+int32_t lds_debug_pick_next(int32_t nq, const int64_t* bytes, const uint8_t* graph_busy, int64_t free_bytes);
+
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load

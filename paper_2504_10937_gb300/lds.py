@@ -56,6 +56,16 @@ class TopkStats(ctypes.Structure):
                [(f, ctypes.c_double) for f in ("ms_total", "ms_fw", "ms_extract", "ms_prune", "ms_verify")]
 
 
+class Query(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_void_p), ("k", ctypes.c_int32), ("d", ctypes.c_int), ("iters", ctypes.c_int32),
+                ("p", ctypes.c_int)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+                ("stats", TopkStats)]
+
+
 def _sig(lib, name, res, args):
     fn = getattr(lib, name)
     fn.restype = res
@@ -99,6 +109,16 @@ def load():
     _sig(lib, "lds_topk_last_stats", ctypes.c_int, [ctypes.POINTER(TopkStats)])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
                                                ctypes.POINTER(i32), P])
+    _sig(lib, "lds_server_create", ctypes.c_int, [i64, i32, ctypes.POINTER(P)])
+    _sig(lib, "lds_server_submit", ctypes.c_int, [P, ctypes.POINTER(Query), ctypes.POINTER(i64)])
+    _sig(lib, "lds_server_poll", ctypes.c_int, [P, i64, ctypes.POINTER(i32)])
+    _sig(lib, "lds_server_wait", ctypes.c_int, [P, i64, ctypes.POINTER(ctypes.POINTER(LdsResult)),
+                                                ctypes.POINTER(RequestInfo)])
+    _sig(lib, "lds_server_destroy", None, [P])
+    _sig(lib, "lds_topk_batch", ctypes.c_int, [i32, ctypes.POINTER(Query), i32,
+                                               ctypes.POINTER(ctypes.POINTER(LdsResult)), ctypes.POINTER(ctypes.c_int)])
+    _sig(lib, "lds_batch_autotune", ctypes.c_int, [i32, ctypes.POINTER(Query), ctypes.POINTER(i32)])
+    _sig(lib, "lds_debug_pick_next", i32, [i32, P, P, i64])
     _lib = lib
     return lib
 
@@ -159,6 +179,106 @@ def pattern_max_flow(nv: int, patterns, p: int, q: int):
     _check(load().lds_pattern_max_flow(int(nv), len(patterns), _ptr(ptr), _ptr(idx), int(p), int(q),
                                        ctypes.byref(f), _ptr(side)))
     return int(f.value), side[:nv]
+
+
+def _result_list(res):
+    """lds_result -> list of (Fraction density, int32 member array)."""
+    from fractions import Fraction
+    r = res.contents
+    out = []
+    if r.count:
+        total = r.offsets[r.count]
+        verts = np.ctypeslib.as_array(r.vertices, shape=(max(total, 1),))[:total].copy()
+        for i in range(r.count):
+            out.append((Fraction(r.dens_num[i], r.dens_den[i]), verts[r.offsets[i]:r.offsets[i + 1]]))
+    return out
+
+
+def _query(g, k: int, density: str, iters: int, precision: str) -> Query:
+    return Query(g.handle, int(k), DENSITY[density], int(iters), PRECISION[precision])
+
+
+def debug_pick_next(bytes_, busy, free_bytes: int) -> int:
+    """The serving loop's admission rule (see lds_debug_pick_next)."""
+    b = np.ascontiguousarray(bytes_, dtype=np.int64)
+    f = np.ascontiguousarray(busy, dtype=np.uint8)
+    return int(load().lds_debug_pick_next(len(b), _ptr(b), _ptr(f), int(free_bytes)))
+
+
+def topk_batch(queries, workers: int = 0):
+    """Runs queries [(graph, k, density, iters, precision), ...] together
+    (lds_topk_batch).  Returns one result list per query, as Graph.topk."""
+    lib = load()
+    qs = (Query * max(len(queries), 1))(*[_query(*q) for q in queries])
+    res = (ctypes.POINTER(LdsResult) * max(len(queries), 1))()
+    sts = (ctypes.c_int * max(len(queries), 1))()
+    st = lib.lds_topk_batch(len(queries), qs, int(workers), res, sts)
+    try:
+        _check(st)
+        return [_result_list(res[i]) for i in range(len(queries))]
+    finally:
+        for i in range(len(queries)):
+            if res[i]:
+                lib.lds_result_free(res[i])
+
+
+def batch_autotune(queries) -> int:
+    qs = (Query * max(len(queries), 1))(*[_query(*q) for q in queries])
+    w = ctypes.c_int32()
+    _check(load().lds_batch_autotune(len(queries), qs, ctypes.byref(w)))
+    return int(w.value)
+
+
+class Server:
+    """The serving loop (lds_server_*): submit() queues a query and returns a
+    ticket at once; wait() blocks for its result and timing."""
+
+    def __init__(self, budget_bytes: int, workers: int):
+        h = ctypes.c_void_p()
+        _check(load().lds_server_create(int(budget_bytes), int(workers), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, g, k: int, density: str = "edge", iters: int = 100, precision: str = "exact") -> int:
+        q = _query(g, k, density, iters, precision)
+        t = ctypes.c_int64()
+        _check(load().lds_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)))
+        return int(t.value)
+
+    def done(self, ticket: int) -> bool:
+        d = ctypes.c_int32()
+        _check(load().lds_server_poll(self._h, int(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def wait(self, ticket: int):
+        lib = load()
+        res = ctypes.POINTER(LdsResult)()
+        info = RequestInfo()
+        st = lib.lds_server_wait(self._h, int(ticket), ctypes.byref(res), ctypes.byref(info))
+        try:
+            _check(st)
+            timing = {"queue_ms": info.queue_ms, "run_ms": info.run_ms, "footprint_bytes": info.footprint_bytes,
+                      "stats": {f: getattr(info.stats, f) for f, _ in TopkStats._fields_}}
+            return _result_list(res), timing
+        finally:
+            if res:
+                lib.lds_result_free(res)
+
+    def close(self):
+        if self._h is not None:
+            load().lds_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def topk_last_stats() -> dict:

@@ -1,0 +1,46 @@
+"""Host logic of the batch and serving layer, without a GPU: the admission
+rule (oldest queued request whose graph is idle and whose footprint fits the
+free budget) and the refusal to start without a device."""
+import numpy as np
+import pytest
+
+from paper_2504_10937_gb300 import lds
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lds.load()
+    return lds
+
+
+def test_pick_oldest_that_fits(lib):
+    assert lib.debug_pick_next([10, 5, 3], [0, 0, 0], 100) == 0
+    assert lib.debug_pick_next([10, 5, 3], [0, 0, 0], 5) == 1
+    assert lib.debug_pick_next([10, 5, 3], [0, 0, 0], 4) == 2
+    assert lib.debug_pick_next([10, 5, 3], [0, 0, 0], 2) == -1
+
+
+def test_pick_skips_busy_graphs(lib):
+    assert lib.debug_pick_next([1, 1, 1], [1, 0, 0], 10) == 1
+    assert lib.debug_pick_next([1, 1, 1], [1, 1, 0], 10) == 2
+    assert lib.debug_pick_next([1, 1, 1], [1, 1, 1], 10) == -1
+    assert lib.debug_pick_next([], [], 10) == -1
+
+
+def test_pick_matches_a_plain_restatement(lib):
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        k = int(rng.integers(1, 12))
+        b = rng.integers(1, 100, k)
+        busy = rng.integers(0, 2, k)
+        free = int(rng.integers(0, 120))
+        want = next((i for i in range(k) if not busy[i] and b[i] <= free), -1)
+        assert lib.debug_pick_next(b, busy, free) == want
+
+
+def test_no_device_means_no_server(lib):
+    if lib.device_count() > 0:
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(lib.LdsError) as e:
+        lib.Server(1 << 30, 2)
+    assert e.value.status == lib.ECUDA
