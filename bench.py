@@ -348,6 +348,137 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _sets(res):
+    return [(str(d), tuple(int(x) for x in c)) for d, c in res]
+
+
+def run_batch(args):
+    """Many small graphs in one batch (lds_topk_batch), against the same
+    queries run one at a time in binary64 (the plain path)."""
+    import torch
+    from paper_2504_10937_gb300 import lds
+    torch.cuda.set_device(0)
+    lds.load()
+    t0 = time.perf_counter()
+    mix = synth.batched_mix(args.graphs, seed=4)
+    gen_s = time.perf_counter() - t0
+    graphs = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
+    queries = [(g, 3, "triangle" if x["triangle"] else "edge", 200 if x["triangle"] else 100, "fp32")
+               for g, x in zip(graphs, mix)]
+    for q in queries:
+        if q[2] == "triangle":
+            q[0].list_triangles()
+    workers = lds.batch_autotune(queries)
+    for _ in range(args.warmup):
+        lds.topk_batch(queries[:64], workers=workers)
+    torch.cuda.synchronize()
+    times, launches0 = [], lds.launch_count()
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            got = lds.topk_batch(queries, workers=workers)
+            times.append(time.perf_counter() - t)
+    launches = lds.launch_count() - launches0
+    sample = min(len(queries), args.plain_sample)
+    t = time.perf_counter()
+    plain = [g.topk(k, d, it, "fp64") for g, k, d, it, _ in queries[:sample]]
+    plain_s = time.perf_counter() - t
+    t = time.perf_counter()
+    serial = [g.topk(k, d, it, p) for g, k, d, it, p in queries[:sample]]
+    serial_s = time.perf_counter() - t
+    same = all(_sets(a) == _sets(b) for a, b in zip(plain, got[:sample]))
+    same_serial = all(_sets(a) == _sets(b) for a, b in zip(serial, got[:sample]))
+    qps = len(queries) * args.steps / sum(times)
+    line = {
+        "metric": "LDS queries/s (batched)", "value": qps, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched_mix: {len(queries)} graphs, n log-uniform in [50, 20000], Chung-Lu "
+                               "exponent 2.3, average degree 8, 1-4 blocks of 10-100 at 0.6-0.95 (seed 4)",
+                   "graphs": len(queries), "triangle_queries": sum(q[2] == "triangle" for q in queries),
+                   "k": 3, "iters": "100 edge / 200 triangle", "precision": "fp32", "workers": workers,
+                   "generation_s": gen_s},
+        "plain_fp64_gpu": {"queries_per_s": sample / plain_s, "sample": sample, "same_output": same},
+        "serial_fp32_gpu": {"queries_per_s": sample / serial_s, "sample": sample, "same_output": same_serial},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+
+
+def run_serve(args):
+    """Poisson stream of top-k queries over a resident graph mix through the
+    serving loop (lds_server_*): queries/s and p50 / p99 latency."""
+    import threading as th
+    import torch
+    from paper_2504_10937_gb300 import lds
+    torch.cuda.set_device(0)
+    lds.load()
+    rng = synth.SplitMix64(5)
+    lo, hi = np.log(1e3), np.log(args.serve_max_n)
+    graphs = []
+    for i in range(args.serve_graphs):
+        n = int(round(np.exp(lo + rng.uniform(1)[0] * (hi - lo))))
+        expo = 2.1 + 0.4 * rng.uniform(1)[0]
+        nn, u, v, _ = synth.chung_lu(n, 5 * n, expo, int(rng.u64(1)[0]), n_blocks=2, block_size_range=(10, 100),
+                                     block_prob_range=(0.6, 0.95), block_size_dist="uniform")
+        g = lds.Graph(nn, u.astype(np.int32), v.astype(np.int32))
+        g.list_triangles()
+        graphs.append(g)
+    reqs = []
+    for i in range(args.requests):
+        g = graphs[int(rng.integers(0, len(graphs), 1)[0])]
+        tri = rng.uniform(1)[0] < 0.3
+        reqs.append((g, int(rng.integers(1, 21, 1)[0]), "triangle" if tri else "edge", 200 if tri else 100, "fp32"))
+    gaps = -np.log(1.0 - rng.uniform(len(reqs))) / args.rate
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    with lds.Server(budget, args.serve_workers) as srv:
+        for r in reqs[:8]:                                 # warm-up
+            srv.wait(srv.submit(*r))
+        tickets = [None] * len(reqs)
+        t_start = time.perf_counter()
+
+        def feeder():
+            t = t_start
+            for i, r in enumerate(reqs):
+                t += gaps[i]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = srv.submit(*r)
+
+        f = th.Thread(target=feeder)
+        with ClockSampler(0) as clk:
+            f.start()
+            lat = []
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0005)
+                _, info = srv.wait(tickets[i])
+                lat.append(info["queue_ms"] + info["run_ms"])
+            f.join()
+            t_end = time.perf_counter()
+    lat.sort()
+    line = {
+        "metric": "LDS queries/s (served)", "value": len(reqs) / (t_end - t_start), "unit": "queries/s",
+        "n_gpus": 1, "steps": len(reqs), "warmup": 8, "ms_per_step": statistics.mean(lat),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(graphs)} resident Chung-Lu graphs, n log-uniform in [1e3, {args.serve_max_n:g}], "
+                               "exponent U(2.1, 2.5), average degree 10, 2 blocks each (seed 5)",
+                   "requests": len(reqs), "arrival_rate_per_s": args.rate, "k": "uniform 1-20",
+                   "edge_triangle": "70:30", "precision": "fp32", "workers": args.serve_workers,
+                   "budget_bytes": budget},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))],
+                       "max": lat[-1]},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,7 +493,22 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the binary64 comparison queries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--mode", choices=["query", "batch", "serve"], default="query",
+                    help="query: the headline line; batch / serve: the many-query layers")
+    ap.add_argument("--graphs", type=int, default=4096, help="batch mode: number of graphs")
+    ap.add_argument("--plain-sample", type=int, default=64, help="batch mode: queries run one at a time")
+    ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
+    ap.add_argument("--rate", type=float, default=40.0, help="serve mode: Poisson arrivals per second")
+    ap.add_argument("--serve-graphs", type=int, default=16)
+    ap.add_argument("--serve-max-n", type=float, default=1e5)
+    ap.add_argument("--serve-workers", type=int, default=8)
     args = ap.parse_args()
+    if args.mode == "batch" and args.impl == "ours":
+        run_batch(args)
+        return
+    if args.mode == "serve" and args.impl == "ours":
+        run_serve(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
