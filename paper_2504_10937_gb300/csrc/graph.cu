@@ -347,6 +347,37 @@ static void build_graph(lds_graph* g, int32_t n, int64_t m_in, const int32_t* sr
     g->info.isolated = n - g->nact;
 }
 
+void set_stream(lds_graph* g, cudaStream_t s) {
+    g->stream = s;
+    g->to_orig.s = s;
+    g->to_int.s = s;
+    g->eu.s = s;
+    g->ev.s = s;
+    g->rowptr.s = s;
+    g->col.s = s;
+    g->fwcol.s = s;
+    g->chunk_row0.s = s;
+    g->slot_edge.s = s;
+    g->ta.s = s;
+    g->tb.s = s;
+    g->tc.s = s;
+    g->vt_ptr.s = s;
+    g->vt_idx.s = s;
+    g->fwv_perm.s = s;
+    g->fwv_pos.s = s;
+    g->fwv_col.s = s;
+    g->fwv_nzrow.s = s;
+    g->fwv_chunk_nz0.s = s;
+    g->fwv_edge.s = s;
+    g->fwv_ta.s = s;
+    g->fwv_tb.s = s;
+    g->fwv_tc.s = s;
+    g->fw_R.s = s;
+    g->fw_r.s = s;
+    g->fw_W.s = s;
+    g->fw_last.s = s;
+}
+
 }  // namespace lds
 
 using namespace lds;

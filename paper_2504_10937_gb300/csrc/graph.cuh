@@ -65,6 +65,11 @@ struct lds_graph {
 
 namespace lds {
 
+// Points the handle and every buffer it owns at stream s: later work and the
+// buffers' stream-ordered frees then follow s.  The caller makes sure that no
+// work on the previous stream is pending.
+void set_stream(lds_graph* g, cudaStream_t s);
+
 // Builds slot_edge (canonical edge id of every CSR slot) if not present.
 void ensure_slot_edge(lds_graph* g);
 

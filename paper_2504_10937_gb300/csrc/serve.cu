@@ -8,8 +8,11 @@
 // among the admissible requests the oldest goes first (continuous batching:
 // requests join as slots and memory free up and leave when they finish, and
 // their kernels overlap on the device through the separate streams).  While a
-// worker runs a request it points the handle at its own stream and puts the
-// handle's stream back afterwards.  The paper has no counterpart to this
+// worker runs a request it points the handle, and every buffer the handle
+// owns, at its own stream, and afterwards back at the handle's stream: the
+// buffers free themselves on the stream they follow, so a free is always
+// ordered after the work that used the buffer and never names a worker stream
+// that no longer exists.  The paper has no counterpart to this
 // layer: it only schedules queries the paper defines.
 #include <chrono>
 #include <condition_variable>
@@ -110,12 +113,14 @@ struct lds_server {
             r.error = "lds_server: the graph's stream reported an error";
             return;
         }
-        g->stream = ws;
+        // the handle and its buffers follow the worker's stream during the query,
+        // so that every stream-ordered free is ordered after the work that used it
+        set_stream(g, ws);
         st = lds_topk(g, r.q.k, r.q.d, r.q.iters, r.q.p, &r.result);
         if (st != LDS_OK) r.error = lds_last_error();
         else lds_topk_last_stats(&r.stats);
         cudaStreamSynchronize(ws);
-        g->stream = old;
+        set_stream(g, old);
         r.status = st;
     }
 
