@@ -40,9 +40,9 @@ METRIC = "FW edge-updates/s"
 UNIT = "edge-updates/s"
 
 # DRAM bytes (read + write) of one launch of the pass kernel on this workload, from
-# one ncu capture of the current kernel (see profiles/); a kernel changed since
-# then has no entry and reports null.
-PASS_TRAFFIC = {}
+# one ncu capture of the current kernel (profiles/fw_opass32_chung_lu_1m.md); a
+# kernel changed since then has no entry and reports null.
+PASS_TRAFFIC = {("fw_opass32_kernel", "exact"): 20494336}
 
 
 def _peaks():
