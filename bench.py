@@ -127,6 +127,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def job_rate(total_ms: float, units: int, device=None):
+    """Whole-job rate over the ranks of the process group (if any): the units of
+    every rank summed, over the slowest rank's time.  Returns (rate per second,
+    job ms, job units)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / (total_ms / 1000.0), total_ms, units
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1000.0), float(t.item()), int(u.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,13 +271,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     m = m_holder["m"]
-    total_ms = sum(times)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    units = sum(updates) * world
-    value = units / (total_ms / 1000.0)
+    value, total_ms, units = job_rate(sum(times), sum(updates), dev)
 
     # end to end through the C-ABI with host (pinned) buffers
     ha = torch.from_numpy(a).pin_memory()
