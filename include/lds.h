@@ -146,6 +146,26 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
  *                  bit-plane word, and one load (key) read per vertex
  *   pass_kernel    name of the pass kernel used (static string)
  * Any pointer may be NULL. */
+/* The current Frank-Wolfe state of the handle (left by lds_fw, lds_fw_batch or
+ * the first round of lds_topk) copied out as lds_fw does: r, R, W in original
+ * ids and canonical order (`last` must be NULL unless the state kept it).
+ * Errors: LDS_EINVAL when the handle holds no state. */
+lds_status lds_fw_state(lds_graph* g, lds_mem where, lds_fw_result* out);
+
+/* Edge-density Frank-Wolfe (Alg. 1) of `iters` iterations on `count` distinct
+ * graphs.  Every graph whose non-isolated vertices fit in shared memory
+ * (at most 24,576, and max degree x D_iters below 2^32; EXACT or FP32) runs
+ * in one persistent launch: one CTA per SM takes graphs from a queue, largest
+ * first, and runs all iterations of a graph with its loads and counts on chip.
+ * The others run as lds_fw does.  Each handle is left with exactly the state
+ * lds_fw(g, LDS_EDGE, iters, p, ...) would leave (same iterates, ties and
+ * rounding), and the next lds_topk on it with the same iterations and
+ * arithmetic takes that state for its first round instead of recomputing it.
+ *   onchip   receives how many graphs ran on chip (may be NULL)
+ * Errors: LDS_EINVAL (NULL or repeated graph, bad iters or precision),
+ * LDS_ENOMEM, LDS_ECUDA. */
+lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p, int32_t* onchip);
+
 lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us,
                               int64_t* pass_launches, int64_t* pass_bytes, const char** pass_kernel);
 
@@ -290,7 +310,9 @@ lds_status lds_server_wait(lds_server* s, int64_t ticket, lds_result** out, lds_
 void lds_server_destroy(lds_server* s);
 
 /* Runs `count` queries with `workers` worker threads (0: the count chosen by
- * lds_batch_autotune) and no memory budget.  results[i] / status[i] belong to
+ * lds_batch_autotune) and no memory budget.  The first rounds of edge-density
+ * queries whose graph appears once in the batch run together first, in
+ * lds_fw_batch's persistent launch.  results[i] / status[i] belong to
  * queries[i]; the return value is the first failure, or LDS_OK. */
 lds_status lds_topk_batch(int32_t count, const lds_query* queries, int32_t workers, lds_result** results,
                           lds_status* status);

@@ -654,6 +654,8 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
     g->pass_us = timer.used ? 1000.0 * timer.total_ms() / (timer.used / 2) : 0.0;
     g->fw_valid = true;
     g->fw_density = d;
+    g->fw_prec = p;
+    g->fw_reuse = false;
     g->fw_iters = iters;
     g->fw_D = Dn;
 }
@@ -673,6 +675,28 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
                     "lds_fw: iters = %d out of range", iters);
         LDS_REQUIRE(where == LDS_MEM_HOST || where == LDS_MEM_DEVICE, LDS_EINVAL, "lds_fw: bad lds_mem");
         fw_run(g, d, iters, p, out->last != nullptr);
+        copy_fw_state(g, d, where, out);
+    });
+}
+
+lds_status lds_fw_state(lds_graph* g, lds_mem where, lds_fw_result* out) {
+    return guard([&] {
+        LDS_REQUIRE(g && out, LDS_EINVAL, "lds_fw_state: NULL argument");
+        LDS_REQUIRE(g->fw_valid, LDS_EINVAL, "lds_fw_state: no Frank-Wolfe state on this graph");
+        LDS_REQUIRE(where == LDS_MEM_HOST || where == LDS_MEM_DEVICE, LDS_EINVAL, "lds_fw_state: bad lds_mem");
+        LDS_REQUIRE(out->last == nullptr || g->fw_last.get() != nullptr, LDS_EINVAL,
+                    "lds_fw_state: the last choices were not kept for this state");
+        copy_fw_state(g, g->fw_density, where, out);
+    });
+}
+
+}  // extern "C"
+
+namespace lds {
+
+// r, R, W (and the last choices) of the handle's state into the caller's buffers
+void copy_fw_state(lds_graph* g, lds_density d, lds_mem where, lds_fw_result* out) {
+    {
         cudaStream_t s = g->stream;
         const int32_t n = g->n;
         out->D = g->fw_D;
@@ -692,8 +716,12 @@ lds_status lds_fw(lds_graph* g, lds_density d, int32_t iters, lds_precision p, l
         if (out->W && npat) copy_out(out->W, where, g->fw_W.get(), (d == LDS_EDGE ? 1 : 3) * npat * sizeof(int64_t), s);
         if (out->last && npat) copy_out(out->last, where, g->fw_last.get(), npat, s);
         LDS_CUDA(cudaStreamSynchronize(s));
-    });
+    }
 }
+
+}  // namespace lds
+
+extern "C" {
 
 lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us, int64_t* pass_launches,
                               int64_t* pass_bytes, const char** pass_kernel) {

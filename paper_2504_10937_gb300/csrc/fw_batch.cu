@@ -1,0 +1,208 @@
+// Frank-Wolfe (Alg. 1, edge density) for many small graphs in one persistent
+// launch.
+//
+// One CTA of 1024 threads per SM takes graphs from a shared queue (largest
+// first).  A graph whose active vertices fit in shared memory (8 bytes each:
+// a 32-bit load word and a 32-bit count) runs all N iterations there: per
+// iteration every edge (u, v), u < v, goes to the endpoint with the smaller
+// load (ties to v, the larger id), counts are added in shared memory, then
+// every load is updated: exact R <- R + 2(i+1) c, or binary32
+// r <- (1 - gamma) r + gamma c with gamma = 2 / (i + 2) and each operation
+// rounded on its own.  W = D_i alpha of the edge's lower endpoint grows by
+// 2(i+1) whenever u takes the edge.  These are the same iterates, the same
+// tie rule and the same rounding as the single-graph path, so the state left
+// in each handle is identical to what lds_fw would leave: W and R = D_N r as
+// exact integers, r in binary64.  Graphs that do not fit run the single-graph
+// path.
+#include <algorithm>
+#include <chrono>
+#include <unordered_set>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace lds {
+
+namespace {
+
+constexpr int FB_THREADS = 1024;
+constexpr int32_t ONCHIP_MAX_V = 24576;          // 8 B of shared memory per vertex
+
+struct GraphJob {
+    const int32_t* eu;
+    const int32_t* ev;
+    const int64_t* rowptr;
+    int64_t m;
+    int32_t nact, n;
+    uint32_t* wt;       // [m] working W (32 bits)
+    int64_t* W;         // [m] out: W per canonical edge
+    int64_t* R;         // [n] out: exact loads
+    double* r;          // [n] out: reported loads
+};
+
+template <bool FP32>
+__global__ void __launch_bounds__(FB_THREADS, 1)
+    fw_batch_kernel(const GraphJob* __restrict__ jobs, int32_t njobs, int32_t* next, int32_t N) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    __shared__ int32_t job;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (;;) {
+        if (tid == 0) job = atomicAdd(next, 1);
+        __syncthreads();
+        const int32_t j = job;
+        __syncthreads();
+        if (j >= njobs) return;
+        const GraphJob g = jobs[j];
+        const int32_t nv = g.nact;
+        uint32_t* L = sm;          // load words: R, or the bits of r in binary32
+        uint32_t* C = sm + nv;     // counts
+        for (int32_t x = tid; x < nv; x += bd) {
+            const uint32_t d = (uint32_t)(g.rowptr[x + 1] - g.rowptr[x]);
+            L[x] = FP32 ? __float_as_uint(__fmul_rn((float)d, 0.5f)) : d;     // r0 = deg / 2, R0 = D_0 r0 = deg
+            C[x] = 0;
+        }
+        for (int64_t e = tid; e < g.m; e += bd) g.wt[e] = 1u;                // W0 = D_0 / 2
+        __syncthreads();
+        for (int32_t i = 1; i <= N; ++i) {
+            const uint32_t inc = 2u * (uint32_t)(i + 1);
+            for (int64_t e = tid; e < g.m; e += bd) {
+                const int32_t u = g.eu[e], v = g.ev[e];
+                const uint32_t lu = L[u], lv = L[v];
+                const bool to_u = FP32 ? (__uint_as_float(lu) < __uint_as_float(lv)) : (lu < lv);
+                atomicAdd(C + (to_u ? u : v), 1u);
+                if (to_u) g.wt[e] += inc;
+            }
+            __syncthreads();
+            if (FP32) {
+                const float gam = 2.0f / (float)(i + 2);
+                const float om = 1.0f - gam;
+                for (int32_t x = tid; x < nv; x += bd) {
+                    const uint32_t c = C[x];
+                    L[x] = __float_as_uint(__fadd_rn(__fmul_rn(om, __uint_as_float(L[x])), __fmul_rn(gam, (float)c)));
+                    C[x] = 0;
+                }
+            } else {
+                for (int32_t x = tid; x < nv; x += bd) {
+                    const uint32_t c = C[x];
+                    if (c) {
+                        L[x] += inc * c;
+                        C[x] = 0;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // outputs: W, R = the incident shares of W (D_N - W for the upper endpoint), r
+        const uint32_t D = (uint32_t)(N + 1) * (uint32_t)(N + 2);
+        for (int64_t e = tid; e < g.m; e += bd) {
+            const uint32_t w = g.wt[e];
+            g.W[e] = (int64_t)w;
+            atomicAdd(C + g.eu[e], w);
+            atomicAdd(C + g.ev[e], D - w);
+        }
+        __syncthreads();
+        for (int32_t x = tid; x < g.n; x += bd) {
+            if (x < nv) {
+                g.R[x] = (int64_t)C[x];
+                g.r[x] = FP32 ? (double)__uint_as_float(L[x]) : (double)L[x] / (double)D;
+            } else {
+                g.R[x] = 0;
+                g.r[x] = 0.0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+bool fits_on_chip(const lds_graph* g, int32_t N, lds_precision p) {
+    if (p != LDS_EXACT && p != LDS_FP32) return false;
+    if (N < 1 || g->m < 1 || g->nact > ONCHIP_MAX_V) return false;
+    const unsigned __int128 D = (unsigned __int128)(N + 1) * (unsigned __int128)(N + 2);
+    // every load and every share sum must fit 32 bits
+    return (unsigned __int128)std::max(g->info.max_degree, 1) * D < ((unsigned __int128)1 << 32);
+}
+
+}  // namespace
+
+}  // namespace lds
+
+using namespace lds;
+
+extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p,
+                                   int32_t* onchip) {
+    return guard([&] {
+        LDS_REQUIRE(count >= 0 && (count == 0 || graphs), LDS_EINVAL, "lds_fw_batch: bad graph list");
+        LDS_REQUIRE(iters >= 0 && iters <= 60000, LDS_EINVAL, "lds_fw_batch: iters = %d out of range", iters);
+        LDS_REQUIRE(p == LDS_EXACT || p == LDS_FP32 || p == LDS_FP64, LDS_EINVAL, "lds_fw_batch: bad precision");
+        std::unordered_set<const lds_graph*> seen;
+        for (int32_t i = 0; i < count; ++i) {
+            LDS_REQUIRE(graphs[i], LDS_EINVAL, "lds_fw_batch: graph %d is NULL", i);
+            LDS_REQUIRE(seen.insert(graphs[i]).second, LDS_EINVAL, "lds_fw_batch: graph %d appears twice", i);
+        }
+        if (onchip) *onchip = 0;
+        std::vector<lds_graph*> on, off;
+        for (int32_t i = 0; i < count; ++i) (fits_on_chip(graphs[i], iters, p) ? on : off).push_back(graphs[i]);
+        // the rest run the single-graph path
+        for (lds_graph* g : off) {
+            fw_run(g, LDS_EDGE, iters, p, false);
+            g->fw_reuse = true;
+        }
+        if (on.empty()) return;
+        std::sort(on.begin(), on.end(), [](const lds_graph* a, const lds_graph* b) { return a->m > b->m; });
+        // each handle's buffers are allocated on its own stream, then everything runs on the first one
+        int64_t total_m = 0;
+        for (lds_graph* g : on) total_m += g->m;
+        cudaStream_t s = on.front()->stream;
+        DevBuf<uint32_t> wt(total_m, s);
+        std::vector<GraphJob> jobs;
+        int64_t off_m = 0;
+        int32_t maxv = 1;
+        for (lds_graph* g : on) {
+            cudaStream_t gs = g->stream;
+            LDS_CUDA(cudaStreamSynchronize(gs));
+            g->fw_valid = false;
+            g->fw_last.release();
+            g->fw_R.alloc(std::max(g->n, 1), gs);
+            g->fw_r.alloc(std::max(g->n, 1), gs);
+            g->fw_W.alloc(std::max<int64_t>(g->m, 1), gs);
+            LDS_CUDA(cudaStreamSynchronize(gs));
+            jobs.push_back(GraphJob{g->eu.get(), g->ev.get(), g->rowptr.get(), g->m, g->nact, g->n,
+                                   wt.get() + off_m, g->fw_W.get(), g->fw_R.get(), g->fw_r.get()});
+            off_m += g->m;
+            maxv = std::max(maxv, g->nact);
+        }
+        DevBuf<GraphJob> djobs(jobs.size(), s);
+        DevBuf<int32_t> next(1, s);
+        LDS_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), jobs.size() * sizeof(GraphJob), cudaMemcpyHostToDevice, s));
+        LDS_CUDA(cudaMemsetAsync(next.get(), 0, sizeof(int32_t), s));
+        const size_t smem = (size_t)maxv * 8;
+        const int grid = std::max(1, std::min(num_sms(), (int)jobs.size()));
+        const auto t0 = std::chrono::steady_clock::now();
+        if (p == LDS_FP32) {
+            LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LDS_LAUNCH(fw_batch_kernel<true>, grid, FB_THREADS, smem, s, djobs.get(), (int32_t)jobs.size(), next.get(),
+                       iters);
+        } else {
+            LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            LDS_LAUNCH(fw_batch_kernel<false>, grid, FB_THREADS, smem, s, djobs.get(), (int32_t)jobs.size(), next.get(),
+                       iters);
+        }
+        LDS_CUDA(cudaStreamSynchronize(s));
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        const int64_t Dn = (int64_t)(iters + 1) * (iters + 2);
+        for (lds_graph* g : on) {
+            g->fw_valid = true;
+            g->fw_density = LDS_EDGE;
+            g->fw_prec = p;
+            g->fw_iters = iters;
+            g->fw_D = Dn;
+            g->fw_reuse = true;
+            g->fw_ms = ms;
+            g->pass_us = 0.0;
+            g->pass_launches = 0;
+            g->pass_bytes = 0;
+            g->pass_kernel = "fw_batch_kernel";
+        }
+        if (onchip) *onchip = (int32_t)on.size();
+    });
+}

@@ -49,6 +49,8 @@ struct lds_graph {
     // state of the most recent Frank-Wolfe run (internal ids), read by the later stages
     bool fw_valid = false;
     lds_density fw_density = LDS_EDGE;
+    lds_precision fw_prec = LDS_EXACT;
+    bool fw_reuse = false;            // set by lds_fw_batch: the next query's first round takes this state
     int32_t fw_iters = 0;
     int64_t fw_D = 0;
     lds::DevBuf<int64_t> fw_R;        // [n] exact loads of the weights below (R = D r)
@@ -75,6 +77,9 @@ void ensure_slot_edge(lds_graph* g);
 
 // Runs `iters` Frank-Wolfe iterations and leaves the results in g->fw_*.
 void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool want_last);
+
+// Copies r, R, W (and the last choices when asked) of the handle's state out.
+void copy_fw_state(lds_graph* g, lds_density d, lds_mem where, lds_fw_result* out);
 
 // Builds the FW view (see lds_graph) if not present.
 void ensure_fw_view(lds_graph* g);

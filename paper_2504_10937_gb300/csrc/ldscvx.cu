@@ -240,7 +240,12 @@ struct Driver {
     void round(lds_graph* h, Bounds& b, int32_t iters, DevBuf<int32_t>& members, std::vector<int64_t>& offs) {
         cudaStream_t s = h->stream;
         auto t0 = std::chrono::steady_clock::now();
-        fw_run(h, tri ? LDS_TRIANGLE : LDS_EDGE, iters, prec, false);
+        // a state left by lds_fw_batch for exactly this round is taken as it is
+        const lds_density dd = tri ? LDS_TRIANGLE : LDS_EDGE;
+        const bool reuse = h->fw_reuse && h->fw_valid && h->fw_density == dd && h->fw_iters == iters &&
+                           h->fw_prec == prec;
+        h->fw_reuse = false;
+        if (!reuse) fw_run(h, dd, iters, prec, false);
         ++stats.fw_rounds;
         stats.fw_edge_updates += (tri ? h->ntri : h->m) * (int64_t)iters;
         auto t1 = std::chrono::steady_clock::now();

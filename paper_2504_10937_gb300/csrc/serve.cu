@@ -301,6 +301,24 @@ lds_status lds_topk_batch(int32_t count, const lds_query* queries, int32_t worke
         if (st != LDS_OK) return st;
         workers = w;
     }
+    // First rounds of the edge-density queries in one persistent launch: every
+    // graph that appears in exactly one query of the batch, grouped by
+    // (iterations, arithmetic); the queries then take that state as it is.
+    {
+        std::unordered_map<const lds_graph*, int32_t> uses;
+        for (int32_t i = 0; i < count; ++i) ++uses[queries[i].g];
+        std::unordered_map<int64_t, std::vector<lds_graph*>> groups;
+        for (int32_t i = 0; i < count; ++i) {
+            const lds_query& q = queries[i];
+            if (q.d != LDS_EDGE || uses[q.g] != 1) continue;
+            groups[((int64_t)q.iters << 2) | (int64_t)q.p].push_back(q.g);
+        }
+        for (auto& kv : groups) {
+            st = lds_fw_batch((int32_t)kv.second.size(), kv.second.data(), (int32_t)(kv.first >> 2),
+                              (lds_precision)(kv.first & 3), nullptr);
+            if (st != LDS_OK) return st;
+        }
+    }
     lds_server* s = nullptr;
     st = lds_server_create(INT64_MAX, workers, &s);
     if (st != LDS_OK) return st;

@@ -109,6 +109,8 @@ def load():
     _sig(lib, "lds_topk_last_stats", ctypes.c_int, [ctypes.POINTER(TopkStats)])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
                                                ctypes.POINTER(i32), P])
+    _sig(lib, "lds_fw_state", ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(FwResult)])
+    _sig(lib, "lds_fw_batch", ctypes.c_int, [i32, ctypes.POINTER(P), i32, ctypes.c_int, ctypes.POINTER(i32)])
     _sig(lib, "lds_server_create", ctypes.c_int, [i64, i32, ctypes.POINTER(P)])
     _sig(lib, "lds_server_submit", ctypes.c_int, [P, ctypes.POINTER(Query), ctypes.POINTER(i64)])
     _sig(lib, "lds_server_poll", ctypes.c_int, [P, i64, ctypes.POINTER(i32)])
@@ -220,6 +222,15 @@ def topk_batch(queries, workers: int = 0):
         for i in range(len(queries)):
             if res[i]:
                 lib.lds_result_free(res[i])
+
+
+def fw_batch(graphs, iters: int, precision: str = "exact") -> int:
+    """Edge-density Frank-Wolfe on many graphs (lds_fw_batch); returns how
+    many ran in the on-chip persistent launch."""
+    hs = (ctypes.c_void_p * max(len(graphs), 1))(*[g.handle.value for g in graphs])
+    on = ctypes.c_int32()
+    _check(load().lds_fw_batch(len(graphs), hs, int(iters), PRECISION[precision], ctypes.byref(on)))
+    return int(on.value)
 
 
 def batch_autotune(queries) -> int:
@@ -382,6 +393,19 @@ class Graph:
             res.last = out["last"].ctypes.data
         _check(load().lds_fw(self._h, DENSITY[density], int(iters), PRECISION[precision], MEM_HOST,
                              ctypes.byref(res)))
+        out["D"] = int(res.D)
+        return out
+
+    def fw_state(self):
+        """The handle's current Frank-Wolfe state (edge density): r, R, W, D."""
+        out = {"r": np.empty(self.n, dtype=np.float64), "R": np.empty(self.n, dtype=np.int64),
+               "W": np.empty(max(self.m, 1), dtype=np.int64)}
+        res = FwResult()
+        res.r = out["r"].ctypes.data
+        res.R = out["R"].ctypes.data
+        res.W = out["W"].ctypes.data
+        _check(load().lds_fw_state(self._h, MEM_HOST, ctypes.byref(res)))
+        out["W"] = out["W"][:self.m]
         out["D"] = int(res.D)
         return out
 

@@ -32,6 +32,27 @@ def _same(a, b):
         assert np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("precision", ["exact", "fp32"])
+def test_fw_batch_state_equals_single_graph_path(lds, precision):
+    mix = synth.batched_mix(20, seed=407, n_range=(40, 3000))
+    n, u, v, _ = synth.chung_lu(30000, 90000, 2.3, seed=408)    # too many vertices for the on-chip kernel
+    mix.append(dict(n=n, u=u, v=v, triangle=False))
+    iters = 37
+    batch = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
+    single = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
+    on = lds.fw_batch(batch, iters, precision)
+    assert on == len(mix) - 1
+    for a, b in zip(batch, single):
+        got = a.fw_state()
+        want = b.fw(iters, precision=precision, want=("r", "R", "W"))
+        assert got["D"] == want["D"]
+        assert np.array_equal(got["R"], want["R"])
+        assert np.array_equal(got["W"], want["W"])
+        assert np.array_equal(got["r"], want["r"])
+    for g in batch + single:
+        g.close()
+
+
 def test_batch_equals_single_queries(lds):
     gs = _graphs(lds, 24, seed=401)
     queries = [(g, 3, d, 60, "fp32") for g, d in gs]
