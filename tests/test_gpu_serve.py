@@ -41,7 +41,10 @@ def test_fw_batch_state_equals_single_graph_path(lds, precision):
     batch = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
     single = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
     on = lds.fw_batch(batch, iters, precision)
-    assert on == len(mix) - 1
+    D = (iters + 1) * (iters + 2)
+    fits = [g.info()["n"] - g.info()["isolated"] <= 24576 and g.m > 0 and
+            max(g.info()["max_degree"], 1) * D < 2 ** 32 for g in batch]
+    assert on == sum(fits) and not fits[-1]
     for a, b in zip(batch, single):
         got = a.fw_state()
         want = b.fw(iters, precision=precision, want=("r", "R", "W"))
