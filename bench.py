@@ -440,12 +440,13 @@ def run_serve(args):
         g = graphs[int(rng.integers(0, len(graphs), 1)[0])]
         tri = rng.uniform(1)[0] < 0.3
         reqs.append((g, int(rng.integers(1, 21, 1)[0]), "triangle" if tri else "edge", 200 if tri else 100, "fp32"))
-    gaps = -np.log(1.0 - rng.uniform(len(reqs))) / args.rate
+    unit_gaps = -np.log(1.0 - rng.uniform(len(reqs)))
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    with lds.Server(budget, args.serve_workers) as srv:
-        for r in reqs[:8]:                                 # warm-up
-            srv.wait(srv.submit(*r))
+
+    def run_at(srv, rate):
+        """Open-loop Poisson arrivals at `rate`; returns (queries/s, sorted latencies)."""
+        gaps = unit_gaps / rate
         tickets = [None] * len(reqs)
         t_start = time.perf_counter()
 
@@ -459,19 +460,32 @@ def run_serve(args):
                 tickets[i] = srv.submit(*r)
 
         f = th.Thread(target=feeder)
+        f.start()
+        lat = []
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            _, info = srv.wait(tickets[i])
+            lat.append(info["queue_ms"] + info["run_ms"])
+        f.join()
+        return len(reqs) / (time.perf_counter() - t_start), sorted(lat)
+
+    def pct(lat, q):
+        return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
+
+    sweep = []
+    with lds.Server(budget, args.serve_workers) as srv:
+        for r in reqs[:8]:                                 # warm-up
+            srv.wait(srv.submit(*r))
         with ClockSampler(0) as clk:
-            f.start()
-            lat = []
-            for i in range(len(reqs)):
-                while tickets[i] is None:
-                    time.sleep(0.0005)
-                _, info = srv.wait(tickets[i])
-                lat.append(info["queue_ms"] + info["run_ms"])
-            f.join()
-            t_end = time.perf_counter()
-    lat.sort()
+            qps, lat = run_at(srv, args.rate)
+            # offered load below saturation: fractions of the rate just measured
+            for frac in ([] if args.no_sweep else [0.25, 0.5, 0.75, 0.9]):
+                q2, l2 = run_at(srv, frac * qps)
+                sweep.append({"offered_per_s": frac * qps, "queries_per_s": q2, "p50_ms": pct(l2, 0.5),
+                              "p99_ms": pct(l2, 0.99)})
     line = {
-        "metric": "LDS queries/s (served)", "value": len(reqs) / (t_end - t_start), "unit": "queries/s",
+        "metric": "LDS queries/s (served)", "value": qps, "unit": "queries/s",
         "n_gpus": 1, "steps": len(reqs), "warmup": 8, "ms_per_step": statistics.mean(lat),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{len(graphs)} resident Chung-Lu graphs, n log-uniform in [1e3, {args.serve_max_n:g}], "
@@ -479,8 +493,8 @@ def run_serve(args):
                    "requests": len(reqs), "arrival_rate_per_s": args.rate, "k": "uniform 1-20",
                    "edge_triangle": "70:30", "precision": "fp32", "workers": args.serve_workers,
                    "budget_bytes": budget},
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))],
-                       "max": lat[-1]},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": lat[-1]},
+        "offered_load_sweep": sweep,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -511,6 +525,7 @@ def main():
     ap.add_argument("--serve-graphs", type=int, default=16)
     ap.add_argument("--serve-max-n", type=float, default=1e5)
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--no-sweep", action="store_true", help="serve mode: skip the offered-load sweep")
     args = ap.parse_args()
     if args.mode == "batch" and args.impl == "ours":
         run_batch(args)
