@@ -44,3 +44,32 @@ def test_no_device_means_no_server(lib):
     with pytest.raises(lib.LdsError) as e:
         lib.Server(1 << 30, 2)
     assert e.value.status == lib.ECUDA
+
+
+class _NoGraph:
+    """A stand-in handle: the entry points must reject it before any device work."""
+    def __init__(self, value):
+        import ctypes
+        self.handle = ctypes.c_void_p(value)
+
+
+def test_batch_rejects_null_graph(lib):
+    with pytest.raises(lib.LdsError) as e:
+        lib.topk_batch([(_NoGraph(None), 3, "edge", 10, "exact")], workers=1)
+    assert e.value.status == lib.EINVAL
+
+
+def test_fw_batch_rejects_null_and_repeated_graphs(lib):
+    with pytest.raises(lib.LdsError) as e:
+        lib.fw_batch([_NoGraph(None)], 10, "exact")
+    assert e.value.status == lib.EINVAL
+    # the repeat is found before any handle is touched
+    g = _NoGraph(0x1000)
+    with pytest.raises(lib.LdsError) as e:
+        lib.fw_batch([g, g], 10, "exact")
+    assert e.value.status == lib.EINVAL
+    assert "twice" in str(e.value)
+
+
+def test_empty_batch_is_fine(lib):
+    assert lib.topk_batch([], workers=1) == []
