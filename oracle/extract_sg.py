@@ -5,7 +5,7 @@ from Lemma 4 / Lemma 8.  Everything is exact: the feasible solution is given as
 integers W over a common denominator D (alpha = W / D), loads R = D * r, and
 all comparisons are between integers or Fractions.
 
-Readings of the paper (listed in the design doc):
+Readings of the paper:
 
 * Sorting: by r descending, ties by vertex id ascending.
 * Cut points: position i (1-based) is a cut point when density(V[1:i]) is

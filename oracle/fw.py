@@ -1,7 +1,7 @@
 """Frank-Wolfe for the convex programs of the paper (test infrastructure).
 
 Edge program CP(G) (Eq. 2) solved by Alg. 1; triangle program (Eq. 4) solved
-by Alg. 6.  Readings of the paper (each listed in the design doc):
+by Alg. 6.  Readings of the paper:
 
 * Orientation and ties (Alg. 1): every edge is taken as (u, v) with u < v.  The
   paper's test "r_u < r_v" gives the edge to u; otherwise (ties included) it goes

@@ -1,7 +1,7 @@
 """LDScvx / LTDScvx driver (test infrastructure).
 
 Alg. 5 (edge density) and its triangle extension (Sec. 6, "naturally extended"),
-with the readings below (each listed in the design doc):
+with the readings of the paper below:
 
 * Initial reduction (Alg. 5 line 1): ub = core number, lb = core / 2 (edges);
   ub = tr-core, lb = tr-core / 3 (triangles).  A rho-compact graph has minimum

@@ -13,7 +13,7 @@
   triangles); then ExtMaximal; S is an LDS iff it is a connected component of
   the returned vertex set.
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
 
 * The traversal admits w when ub(w) >= rho (text of Sec. 5.4 and the ablation),
   not the strict ">" printed in Alg. 4.
