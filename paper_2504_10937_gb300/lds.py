@@ -412,18 +412,11 @@ class Graph:
     def topk(self, k: int, density: str = "edge", iters: int = 100, precision: str = "exact"):
         """Top-k LDSs (edge) or LTDSs (triangle): list of (Fraction density,
         int32 array of member ids ascending), densest first."""
-        from fractions import Fraction
         lib = load()
         res = ctypes.POINTER(LdsResult)()
         _check(lib.lds_topk(self._h, int(k), DENSITY[density], int(iters), PRECISION[precision], ctypes.byref(res)))
         try:
-            r = res.contents
-            out = []
-            for i in range(r.count):
-                a, b = r.offsets[i], r.offsets[i + 1]
-                verts = np.array([r.vertices[j] for j in range(a, b)], dtype=np.int32)
-                out.append((Fraction(r.dens_num[i], r.dens_den[i]), verts))
-            return out
+            return _result_list(res)
         finally:
             lib.lds_result_free(res)
 

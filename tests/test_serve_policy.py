@@ -73,3 +73,20 @@ def test_fw_batch_rejects_null_and_repeated_graphs(lib):
 
 def test_empty_batch_is_fine(lib):
     assert lib.topk_batch([], workers=1) == []
+
+
+def test_result_conversion(lib):
+    # an lds_result laid out in host memory as the library lays it out
+    import ctypes
+    from fractions import Fraction
+    num = (ctypes.c_int64 * 2)(5, 1)
+    den = (ctypes.c_int64 * 2)(2, 2)
+    off = (ctypes.c_int64 * 3)(0, 3, 5)
+    ver = (ctypes.c_int32 * 5)(1, 4, 7, 2, 3)
+    P64, P32 = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
+    r = lib.LdsResult(2, ctypes.cast(num, P64), ctypes.cast(den, P64), ctypes.cast(off, P64), ctypes.cast(ver, P32))
+    out = lib._result_list(ctypes.pointer(r))
+    assert [(d, c.tolist()) for d, c in out] == [(Fraction(5, 2), [1, 4, 7]), (Fraction(1, 2), [2, 3])]
+    assert all(c.dtype == np.int32 for _, c in out)
+    empty = lib.LdsResult(0, ctypes.cast(num, P64), ctypes.cast(den, P64), ctypes.cast(off, P64), ctypes.cast(ver, P32))
+    assert lib._result_list(ctypes.pointer(empty)) == []
