@@ -27,7 +27,7 @@ Readings of the paper:
 * A candidate that fails is merged with the next one (Alg. 2, loop); a trailing
   remainder that never passes gives no bounds.
 
-Pins (tests/test_oracle_extract_sg.py): on the reconstructed Fig. 1 graph at
+Pins (tests/test_oracle_stages.py): on the reconstructed Fig. 1 graph at
 the optimum the groups are S1, S2, S3, {g, h, i} with Table 2's values; the
 groups partition a prefix of the sorted order; every bound interval contains
 the exact compact number from oracle.decomp (Lemma 4 / Lemma 8) on random

@@ -6,7 +6,7 @@ any exact algorithm gives the same flow value and the same maximal source side
 of a minimum cut, which is the set of nodes that cannot reach the sink in the
 final residual graph (the cut that maximises |A|, proof of Lemma 9).
 
-Pins (tests/test_oracle_flow.py): flow value equals the capacity of the
+Pins (tests/test_oracle_stages.py): flow value equals the capacity of the
 reported cut; value and cut side equal brute force over all s-t cuts on small
 random networks.
 """

@@ -208,10 +208,11 @@ def fw_edge_fp64_literal(n: int, u, v, N: int, record=None):
     return r, a, rowptr, col
 
 
-def fw_tri_fp64_literal(n: int, tris, N: int):
+def fw_tri_fp64_literal(n: int, tris, N: int, record=None):
     """Alg. 6 in binary64 with one alpha per (vertex, triangle).  r_u sums its
     triangles' alphas left to right in ascending triangle order.  Returns
-    (r float64[n], alpha float64 (|T|, 3))."""
+    (r float64[n], alpha float64 (|T|, 3)).  A list passed as ``record``
+    receives the receiving column of every triangle in every iteration."""
     t = np.asarray(tris, dtype=np.int64).reshape(-1, 3)
     a = np.full(t.shape, 1.0 / 3.0, dtype=np.float64)
     # incidence lists in ascending triangle order
@@ -237,6 +238,8 @@ def fw_tri_fp64_literal(n: int, tris, N: int):
         g = _gamma64(i)
         one_minus = 1.0 - g
         x = tri_argmin(r[t]) if len(t) else np.zeros(0, np.int64)
+        if record is not None:
+            record.append(x.copy())
         ah = np.zeros(t.shape, dtype=np.float64)
         ah[rows, x] = 1.0
         a = (one_minus * a) + (g * ah)

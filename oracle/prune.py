@@ -11,7 +11,7 @@ Alg. 3 with Pruning rule 1 (Cor. 1) and Pruning rule 2 (Lemma 5, Lemma 6):
 The loop of rule 2 ends at the largest vertex set X with core_{G[X]}(x) >=
 lb(x) for all x in X, whatever the removal order (core numbers only grow with
 the graph), so this oracle removes all violators of a pass at once.
-Pins (tests/test_oracle_prune.py): the worked example of Sec. 5.2 (r pruned by
+Pins (tests/test_oracle_stages.py): the worked example of Sec. 5.2 (r pruned by
 rule 1; o, p, q, h by rule 2 on the reconstructed Fig. 1 graph); no vertex of
 an LDS from oracle.brute / oracle.decomp is ever removed (Cor. 1, Lemma 5).
 """

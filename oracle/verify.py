@@ -27,7 +27,7 @@ Readings of the paper taken here:
 * The networks of IsDensest and IsLDS are not given in the paper; both use
   Alg. 8's pattern network (edge patterns and loop patterns).
 
-Pins (tests/test_oracle_verify.py, tests/test_oracle_ldscvx.py): IsDensest
+Pins (tests/test_oracle_stages.py, tests/test_oracle_ldscvx.py): IsDensest
 against brute-force densest subgraphs; ExtMaximal against exact compact
 numbers (Lemma 9); IsLDS / IsLTDS with exact bounds against the brute-force
 LDS / LTDS lists on hundreds of small random graphs (Thm. 2, Thm. 5).

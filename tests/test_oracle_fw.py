@@ -124,6 +124,42 @@ def test_fp64_literal_tracks_rational_while_choices_agree():
     assert checked >= 20
 
 
+def test_triangle_fp64_literal_tracks_rational_while_choices_agree():
+    # Alg. 6 in binary64 against the exact integer form (itself pinned to the
+    # rational Alg. 6 above) at every N while the receiving vertices agree: a
+    # summation-order or gamma slip past the first iteration shows up here
+    checked = 0
+    for seed in range(12):
+        n, u, v = random_graph(10, 0.55, seed=800 + seed)
+        tris = graph.triangles(n, u, v)
+        if len(tris) == 0:
+            continue
+        for N in range(1, 10):
+            rec64 = []
+            r64, a = fw.fw_tri_fp64_literal(n, tris, N, record=rec64)
+            R, W, Dn3, rec = fw.fw_tri_exact(n, tris, N, record=True)
+            if _agreeing_prefix(rec64, rec) < N:
+                break
+            checked += 1
+            assert np.allclose(r64, R / Dn3, rtol=1e-13, atol=1e-13)
+            assert np.allclose(a, W / Dn3, rtol=0, atol=1e-14)
+    assert checked >= 20
+
+
+def test_triangle_fp64_literal_against_rational_directly():
+    n, u, v = random_graph(8, 0.6, seed=17)
+    tris = graph.triangles(n, u, v)
+    for N in (2, 3, 5):
+        rec64 = []
+        r64, a = fw.fw_tri_fp64_literal(n, tris, N, record=rec64)
+        r_q, a_q = fw.fw_tri_rational(n, tris, N)
+        _, _, _, rec = fw.fw_tri_exact(n, tris, N, record=True)
+        if _agreeing_prefix(rec64, rec) < N:
+            continue
+        assert np.allclose(r64, [float(x) for x in r_q], rtol=1e-13, atol=1e-13)
+        assert np.allclose(a, np.array([[float(x) for x in row] for row in a_q]), rtol=0, atol=1e-14)
+
+
 def test_fp32_recurrence_tracks_rational_while_choices_agree():
     checked = 0
     for seed in range(12):
