@@ -166,6 +166,14 @@ lds_status lds_fw_state(lds_graph* g, lds_mem where, lds_fw_result* out);
  * LDS_ENOMEM, LDS_ECUDA. */
 lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p, int32_t* onchip);
 
+/* Threads per graph (32 x warps per graph) that lds_fw_batch's persistent launch
+ * uses for graphs of `nact` active vertices: graphs are grouped by size bucket
+ * (the bit length of nact), each bucket launched with shared memory for its
+ * largest graph and as many CTAs per SM as fit.  lds_batch_autotune times 128,
+ * 256, 512 and 1024 threads per graph on its batch, per bucket, and keeps the
+ * fastest for the rest of the process; untuned buckets use 1024.  Never fails. */
+int32_t lds_fw_batch_threads(int32_t nact);
+
 lds_status lds_fw_last_timing(const lds_graph* g, double* fw_ms, double* pass_us,
                               int64_t* pass_launches, int64_t* pass_bytes, const char** pass_kernel);
 
@@ -252,6 +260,36 @@ typedef struct {
  * Errors: LDS_EINVAL, LDS_ENOMEM, LDS_ETIMEOUT, LDS_EOVERFLOW, LDS_ECUDA. */
 lds_status lds_topk(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, lds_result** out);
 
+/* Verification network of IsLDS / IsLTDS (the Sec. 7 ablation).  All three
+ * certify the same sets; they differ in the size of the flow network.
+ *   LDS_VERIFY_BOUNDS  Alg. 4 / Alg. 7: U grows from S over vertices with
+ *                      lb <= rho <= ub; a neighbour with lb > rho rejects S
+ *                      at once, edges to denser outside vertices become loops
+ *                      (the default);
+ *   LDS_VERIFY_CORE    IsLDS-core / IsLTDS-core: U grows over every vertex
+ *                      with ub >= rho; no lower-bound test, no loops;
+ *   LDS_VERIFY_WHOLE   IsLTDS-bs (the LTDSflow baseline), and its edge
+ *                      analogue: the network holds every vertex of G. */
+typedef enum { LDS_VERIFY_BOUNDS = 0, LDS_VERIFY_CORE = 1, LDS_VERIFY_WHOLE = 2 } lds_verify;
+
+/* Per-call options of lds_topk_ex; a NULL pointer means every default. */
+typedef struct {
+    lds_precision prec;             /* FW arithmetic (default LDS_EXACT)                     */
+    void*         cuda_stream;      /* cudaStream_t for this call; NULL: the graph's stream   */
+    int32_t       include_zero_density; /* 1: LDSs of density 0 (isolated vertices; for LTDS
+                                       triangle-free connected sets) count as results (Def. 3
+                                       makes them LDSs); default 0 drops them                  */
+    lds_verify    verify;           /* verification network (default LDS_VERIFY_BOUNDS)      */
+} lds_options;
+
+/* lds_topk with per-call options (Problem 1 / Problem 2 as lds_topk states).
+ * With a stream other than the graph's, the call first waits for the graph's
+ * stream, runs every kernel on the given one and waits for it before returning;
+ * the graph keeps its own stream afterwards.
+ * Errors: as lds_topk; LDS_EINVAL for an unknown precision or verify value. */
+lds_status lds_topk_ex(lds_graph* g, int32_t k, lds_density d, int32_t iters, const lds_options* opt,
+                       lds_result** out);
+
 void lds_result_free(lds_result* r);
 
 lds_status lds_topk_last_stats(lds_topk_stats_t* stats);
@@ -317,9 +355,12 @@ void lds_server_destroy(lds_server* s);
 lds_status lds_topk_batch(int32_t count, const lds_query* queries, int32_t workers, lds_result** results,
                           lds_status* status);
 
-/* Worker count for a batch: times the first min(count, 64) queries with 1, 2,
- * 4, 8 and 16 workers and keeps the fastest; the choice is cached per size
- * bucket (log2 of the mean edge count) for the rest of the process. */
+/* Tuning for a batch.  First the launch shape of the on-chip Frank-Wolfe: for
+ * the batch's edge queries, every size bucket is timed with 128, 256, 512 and
+ * 1024 threads per graph (see lds_fw_batch_threads).  Then the worker count:
+ * the first min(count, 64) queries are timed with 1, 2, 4, 8 and 16 workers and
+ * the fastest is kept.  Both choices are cached (per vertex-count bucket, and
+ * per bucket of log2 of the mean edge count) for the rest of the process. */
 lds_status lds_batch_autotune(int32_t count, const lds_query* queries, int32_t* workers);
 
 /* The admission rule itself, for tests: index of the request the serving loop
@@ -331,11 +372,31 @@ int32_t lds_debug_pick_next(int32_t nq, const int64_t* bytes, const uint8_t* gra
  *   0  automatic: the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load
  *      words when every scaled load fits 32 bits, else with 64-bit keys
- *      (load, id), else variant 1;
+ *      (load, id), else variant 1.  With 32-bit words the pass counts only
+ *      the receipts of the stored targets; the vertex update adds each row
+ *      endpoint's receipts as the popcount of its row's bits in the
+ *      iteration's choice plane, and many iterations (pass, grid barrier,
+ *      update, grid barrier) run in one cooperative launch;
  *   1  the symmetric-CSR pass (each edge twice, once from each endpoint);
- *   2  the degree-oriented pass with 64-bit keys.
+ *   2  the degree-oriented pass with 64-bit keys;
+ *   3  as 0 with 32-bit words, both endpoints' receipts counted inside the
+ *      pass, one pass launch and one update launch per iteration;
+ *   4  as 0 with 32-bit words, one pass launch and one update launch per
+ *      iteration.
  * All compute the same iterates.  Errors: LDS_EINVAL. */
 lds_status lds_set_fw_variant(int32_t variant);
+
+/* Maximum-flow form for the verification networks (process-wide):
+ *   0  automatic: the vertex-node form (2) for every network;
+ *   1  pattern-node form: Alg. 8's network with a node per pattern of three
+ *      members (one- and two-member patterns contracted), asynchronous
+ *      push-relabel with periodic global relabels;
+ *   2  vertex-node form: no pattern nodes; a push moves part of a pattern's
+ *      share from one member to another, in phases of one global relabel and
+ *      one downhill sweep, all in one cooperative launch.
+ * Both return the same maximum flow and the same largest minimum-cut source
+ * side.  Errors: LDS_EINVAL. */
+lds_status lds_set_flow_variant(int32_t variant);
 
 /* Number of CUDA kernels this library has launched since it was loaded
  * (process-wide counter; never fails). */
@@ -363,11 +424,15 @@ void lds_set_pass_profiling(int32_t on);
  *   W        device int64[m], output: (iters+1)(iters+2) alpha_{u,v} per edge
  *   stream   cudaStream_t for all work (NULL: default stream); the call returns
  *            after the stream has finished it
+ * Edges that repeat, or are not sorted by (u, v), are refused with LDS_EINVAL.
  * Scratch: a fixed device array of LDS_NOALLOC_MAX_VERTICES + 64 int32 words,
  * held by every GPU that loads the library until the process exits; the call
  * makes no cudaMalloc / cudaFree or other allocating call.  The first call on
  * each device looks up the array's device address while that device is
- * current; make that first call before any stream capture.  Every call on a
+ * current; make that first call before any stream capture.  The address is
+ * kept per device ordinal for the rest of the process: it assumes the
+ * device's primary context stays alive (no cudaDeviceReset, no other context
+ * made current on that ordinal between calls).  Every call on a
  * device shares the array (each clears what it uses first), so calls that
  * overlap on the GPU race: do not issue them concurrently. */
 lds_status lds_fw_exact_noalloc(int32_t n, int64_t m, const int32_t* u, const int32_t* v, int32_t iters,

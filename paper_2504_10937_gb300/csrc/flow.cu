@@ -43,7 +43,10 @@
 // node needs a label above DEAD, and valid labels of nodes that reach t stay
 // below the node count.  Every loop is bounded; running out of the bound
 // returns LDS_ETIMEOUT.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "flow.cuh"
@@ -293,7 +296,329 @@ int warps_grid(int64_t items) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
+// ---- vertex-node form (no pattern nodes)
+//
+// After the preflow every pattern P holds its qK units split among its members
+// (f_{P,x}).  In Alg. 8's network the residual path x -> P -> y exists exactly
+// when f_{P,x} > 0, and pushing d units along it is f_{P,x} -= d, f_{P,y} += d.
+// So the network needs no pattern nodes: x has a hyper-arc to every other
+// member y of P, all of them drawing on the same capacity f_{P,x}.  Labels
+// stay valid under such a push: if h(x) = h(y) + 1 and the push makes y -> z
+// through P residual for a third member z, then x -> z through P was residual,
+// so h(x) <= h(z) + 1 and h(y) <= h(z).  The vertices that cannot reach t in
+// this residual structure are exactly those that cannot reach t in Alg. 8's
+// network, so the DEAD vertices at the end are the largest source side.
+//
+// Layout: the incidences of every vertex are contiguous (vptr); incidence i
+// holds f (its vertex's share of the pattern) and the incidences / vertices of
+// the pattern's other members (at most two; -1 where absent).  Loops (one
+// member) only feed their vertex and have no incidence.
+struct HNet {
+    int32_t nv;
+    const int64_t* vptr;   // [nv + 1]
+    int64_t* f;            // [ninc]
+    const int32_t* o1;     // [ninc] incidence of another member, -1 if none
+    const int32_t* o2;
+    const int32_t* w1;     // [ninc] vertex of that member, -1 if none
+    const int32_t* w2;
+    int64_t* tcap;         // [nv] residual capacity to t
+    int64_t* excess;       // [nv]
+    int32_t* h;            // [nv] exact distance to t (DEAD: cannot reach it)
+};
+
+// widths above 3 are refused; count[v] = incidences of v; in[v] = flow v receives
+__global__ void hyper_degree_kernel(const int64_t* pptr, const int32_t* pidx, int32_t np, const int64_t* f,
+                                    int32_t* deg, ull* in, int32_t* wide) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        const int64_t b = pptr[j], e = pptr[j + 1], len = e - b;
+        if (len > 3) {
+            *wide = 1;
+            continue;
+        }
+        for (int64_t k = b; k < e; ++k) {
+            atomicAdd(in + pidx[k], (ull)f[k]);
+            if (len >= 2) atomicAdd(deg + pidx[k], 1);
+        }
+    }
+}
+
+// position of every slot (of a pattern with >= 2 members) in its vertex's incidence list
+__global__ void hyper_pos_kernel(const int64_t* pptr, const int32_t* pidx, int32_t np, const int64_t* vptr,
+                                 int32_t* cursor, int32_t* pos) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        const int64_t b = pptr[j], e = pptr[j + 1];
+        if (e - b < 2 || e - b > 3) continue;
+        for (int64_t k = b; k < e; ++k) pos[k] = (int32_t)(vptr[pidx[k]] + atomicAdd(cursor + pidx[k], 1));
+    }
+}
+
+__global__ void hyper_fill_kernel(const int64_t* pptr, const int32_t* pidx, int32_t np, const int64_t* fslot,
+                                  const int32_t* pos, HNet net) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+        const int64_t b = pptr[j], e = pptr[j + 1], len = e - b;
+        if (len < 2 || len > 3) continue;
+        for (int64_t k = b; k < e; ++k) {
+            const int64_t a = k == b ? b + 1 : b;                  // the other members, in slot order
+            const int64_t c = len == 3 ? (k == e - 1 ? e - 2 : e - 1) : -1;
+            const int32_t i = pos[k];
+            net.f[i] = fslot[k];
+            ((int32_t*)net.o1)[i] = pos[a];
+            ((int32_t*)net.w1)[i] = pidx[a];
+            ((int32_t*)net.o2)[i] = c >= 0 ? pos[c] : -1;
+            ((int32_t*)net.w2)[i] = c >= 0 ? pidx[c] : -1;
+        }
+    }
+}
+
+__global__ void hyper_init_kernel(HNet net, const ull* in, int64_t pK, ull* flow_t) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    ull acc = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < net.nv; x += stride) {
+        const int64_t r = (int64_t)in[x];
+        const int64_t toT = min(r, pK);
+        net.tcap[x] = pK - toT;
+        net.excess[x] = r - toT;
+        acc += (ull)toT;
+    }
+    if (acc) atomicAdd(flow_t, acc);
+}
+
+// hyper_flow_kernel control words
+enum : int {
+    HC_LEVEL = 0,      // [0..2] vertices labelled per breadth-first level (three rotating counters)
+    HC_ACTIVE = 3,     // vertices with excess and a label
+    HC_STUCK = 4,      // vertices with excess and no path to t
+    HC_LMAX = 5,       // highest label holding excess
+    HC_FLOW = 6,       // flow into t
+    HC_STATUS = 7,     // 0 finished, 1 phase bound hit, 2 stopped: some excess cannot reach t
+    HC_PHASES = 8,
+    HC_LEVELS = 9,     // breadth-first levels run in all
+    HC_WORDS = 10
+};
+
+// One cooperative launch runs the whole preflow phase.  Each phase computes
+// exact distance labels by a breadth-first search from t over the residual
+// hyper-arcs (a global relabel), then sweeps the labels from the highest one
+// that holds excess down to 1: every vertex at label L with excess pushes it
+// along its admissible hyper-arcs (to members at label L - 1), in incidence
+// order, until the excess or those arcs run out; vertices at label 1 push into
+// t.  Within a label no two vertices touch the same share from below (a share
+// is lowered only by its own vertex, and vertices at label L receive nothing
+// while label L is swept), so a push needs atomics only on the target's share
+// and excess.  After the sweep every vertex that still holds excess has no
+// admissible hyper-arc, and since no push shortens a distance, its label rises
+// in the next phase; labels are at most nv, so there are at most nv^2 + 1
+// phases.  One warp serves one vertex; `max_phases` bounds the loop (status 1).
+__global__ void __launch_bounds__(FB) hyper_flow_kernel(HNet net, ull* ctrl, int64_t max_phases, int stop_if_short) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    const int32_t nv = net.nv;
+    for (int64_t phase = 0;; ++phase) {
+        if (phase >= max_phases) {
+            if (tid == 0) ctrl[HC_STATUS] = 1;
+            return;
+        }
+        if (tid == 0) {
+            ctrl[HC_LEVEL] = ctrl[HC_LEVEL + 1] = ctrl[HC_LEVEL + 2] = 0;
+            ctrl[HC_ACTIVE] = ctrl[HC_STUCK] = ctrl[HC_LMAX] = 0;
+            ctrl[HC_PHASES] = (ull)phase + 1;
+        }
+        for (int64_t v = tid; v < nv; v += nthreads) net.h[v] = __ldcg(net.tcap + v) > 0 ? 1 : DEAD;
+        grid.sync();
+        // breadth-first levels: an unlabelled vertex joins level L + 1 when one of its
+        // hyper-arcs (share > 0) leads to a member at level L
+        for (int32_t L = 1;; ++L) {
+            for (int64_t v = warp; v < nv; v += nwarps) {
+                if (__ldcg(net.h + v) != DEAD) continue;
+                const int64_t b0 = net.vptr[v], b1 = net.vptr[v + 1];
+                bool found = false;
+                for (int64_t base = b0; base < b1 && !found; base += 32) {
+                    const int64_t i = base + lane;
+                    bool hit = false;
+                    if (i < b1 && __ldcg(net.f + i) > 0) {
+                        const int32_t a = net.w1[i], c = net.w2[i];
+                        hit = (a >= 0 && __ldcg(net.h + a) == L) || (c >= 0 && __ldcg(net.h + c) == L);
+                    }
+                    found = __any_sync(FULL, hit);
+                }
+                if (found && lane == 0) {
+                    net.h[v] = L + 1;
+                    atomicAdd(ctrl + HC_LEVEL + (L % 3), 1ull);
+                }
+            }
+            grid.sync();
+            const ull added = __ldcg(ctrl + HC_LEVEL + (L % 3));
+            if (tid == 0) {
+                ctrl[HC_LEVEL + ((L + 2) % 3)] = 0;
+                ctrl[HC_LEVELS] += 1;
+            }
+            if (added == 0) break;
+        }
+        // vertices holding excess: with a label (active) or without (stuck)
+        {
+            ull act = 0, stk = 0;
+            int32_t lmax = 0;
+            for (int64_t v = tid; v < nv; v += nthreads) {
+                if (__ldcg(net.excess + v) > 0) {
+                    const int32_t hv = __ldcg(net.h + v);
+                    if (hv < DEAD) {
+                        ++act;
+                        lmax = max(lmax, hv);
+                    } else {
+                        ++stk;
+                    }
+                }
+            }
+            for (int o = 16; o; o >>= 1) {
+                act += __shfl_xor_sync(FULL, act, o);
+                stk += __shfl_xor_sync(FULL, stk, o);
+                lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
+            }
+            if (lane == 0) {
+                if (act) atomicAdd(ctrl + HC_ACTIVE, act);
+                if (stk) atomicAdd(ctrl + HC_STUCK, stk);
+                if (lmax) atomicMax(ctrl + HC_LMAX, (ull)lmax);
+            }
+        }
+        grid.sync();
+        const ull act = __ldcg(ctrl + HC_ACTIVE), stk = __ldcg(ctrl + HC_STUCK);
+        const int32_t lmax = (int32_t)__ldcg(ctrl + HC_LMAX);
+        if (stop_if_short && stk > 0) {
+            if (tid == 0) ctrl[HC_STATUS] = 2;
+            return;
+        }
+        if (act == 0) {
+            if (tid == 0) ctrl[HC_STATUS] = 0;
+            return;
+        }
+        // downhill sweep
+        for (int32_t L = lmax; L >= 1; --L) {
+            for (int64_t v = warp; v < nv; v += nwarps) {
+                if (__ldcg(net.h + v) != L) continue;
+                const int64_t e = __ldcg(net.excess + v);
+                if (e <= 0) continue;
+                if (L == 1) {
+                    if (lane == 0) {
+                        const int64_t tc = __ldcg(net.tcap + v);
+                        const int64_t d = min(e, tc);
+                        if (d > 0) {
+                            net.tcap[v] = tc - d;
+                            net.excess[v] = e - d;
+                            atomicAdd(ctrl + HC_FLOW, (ull)d);
+                        }
+                    }
+                    continue;
+                }
+                const int64_t b0 = net.vptr[v], b1 = net.vptr[v + 1];
+                int64_t rem = e;
+                for (int64_t base = b0; base < b1 && rem > 0; base += 32) {
+                    const int64_t i = base + lane;
+                    int64_t cap = 0;
+                    int32_t to_i = -1, to_v = -1;
+                    if (i < b1) {
+                        const int64_t fi = __ldcg(net.f + i);
+                        if (fi > 0) {
+                            const int32_t a = net.w1[i], c = net.w2[i];
+                            if (a >= 0 && __ldcg(net.h + a) == L - 1) {
+                                cap = fi;
+                                to_i = net.o1[i];
+                                to_v = a;
+                            } else if (c >= 0 && __ldcg(net.h + c) == L - 1) {
+                                cap = fi;
+                                to_i = net.o2[i];
+                                to_v = c;
+                            }
+                        }
+                    }
+                    // shares of all incidences sum to at most np q K <= 2^61: no overflow
+                    int64_t incl = cap;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int64_t t = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    const int64_t d = max((int64_t)0, min(cap, rem - (incl - cap)));
+                    if (d > 0) {
+                        net.f[i] -= d;
+                        atomicAdd((ull*)(net.f + to_i), (ull)d);
+                        atomicAdd((ull*)(net.excess + to_v), (ull)d);
+                    }
+                    rem -= min(rem, __shfl_sync(FULL, incl, 31));
+                }
+                if (lane == 0 && rem != e) net.excess[v] = rem;
+            }
+            grid.sync();
+        }
+    }
+}
+
 }  // namespace
+
+std::atomic<int> g_flow_variant{0};
+
+// The vertex-node form of the maximum flow, from the split f of every slot.
+static int64_t hyper_max_flow(const int64_t* pptr, const int32_t* pidx, int32_t np, int32_t nv, int64_t nidx,
+                              const int64_t* fslot, int64_t pK, int64_t K, uint8_t* side, bool stop_if_short,
+                              cudaStream_t s) {
+    const int32_t nvp = std::max(nv, 1);
+    DevBuf<int32_t> deg(nvp + 1, s), cursor(nvp, s), wide(1, s);
+    DevBuf<ull> in(nvp, s), ctrl(HC_WORDS, s);
+    LDS_CUDA(cudaMemsetAsync(deg.get(), 0, (nvp + 1) * sizeof(int32_t), s));
+    LDS_CUDA(cudaMemsetAsync(cursor.get(), 0, nvp * sizeof(int32_t), s));
+    LDS_CUDA(cudaMemsetAsync(wide.get(), 0, sizeof(int32_t), s));
+    LDS_CUDA(cudaMemsetAsync(in.get(), 0, nvp * sizeof(ull), s));
+    LDS_CUDA(cudaMemsetAsync(ctrl.get(), 0, HC_WORDS * sizeof(ull), s));
+    if (np)
+        LDS_LAUNCH(hyper_degree_kernel, grid_for(np, FB), FB, 0, s, pptr, pidx, np, fslot, deg.get(), in.get(),
+                   wide.get());
+    DevBuf<int64_t> vptr(nvp + 1, s);
+    const int64_t ninc = exclusive_scan_i32_to_i64(deg.get(), vptr.get(), (int64_t)nv + 1, s);
+    int32_t hwide = 0;
+    LDS_CUDA(cudaMemcpyAsync(&hwide, wide.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    LDS_REQUIRE(hwide == 0, LDS_EINVAL, "max flow: a pattern has more than three members");
+    LDS_REQUIRE(ninc < (int64_t)INT32_MAX, LDS_EOVERFLOW, "max flow: %lld incidences exceed the 32-bit index",
+                (long long)ninc);
+    DevBuf<int32_t> pos(std::max<int64_t>(nidx, 1), s);
+    DevBuf<int64_t> f(std::max<int64_t>(ninc, 1), s), tcap(nvp, s), excess(nvp, s);
+    DevBuf<int32_t> o1(std::max<int64_t>(ninc, 1), s), o2(std::max<int64_t>(ninc, 1), s);
+    DevBuf<int32_t> w1(std::max<int64_t>(ninc, 1), s), w2(std::max<int64_t>(ninc, 1), s), h(nvp, s);
+    HNet net{nv, vptr.get(), f.get(), o1.get(), o2.get(), w1.get(), w2.get(), tcap.get(), excess.get(), h.get()};
+    if (np) {
+        LDS_LAUNCH(hyper_pos_kernel, grid_for(np, FB), FB, 0, s, pptr, pidx, np, vptr.get(), cursor.get(), pos.get());
+        LDS_LAUNCH(hyper_fill_kernel, grid_for(np, FB), FB, 0, s, pptr, pidx, np, fslot, pos.get(), net);
+    }
+    if (nv) LDS_LAUNCH(hyper_init_kernel, grid_for(nv, FB), FB, 0, s, net, in.get(), pK, ctrl.get() + HC_FLOW);
+    if (nv) {
+        int per_sm = 0;
+        LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hyper_flow_kernel, FB, 0));
+        LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "max flow: the flow kernel cannot be resident");
+        // one warp per vertex; no more blocks than can be resident at once
+        const int64_t want = ((int64_t)nv * 32 + FB - 1) / FB;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * std::min(per_sm, 4)));
+        const int64_t max_phases = std::min<int64_t>((int64_t)nv * nv + 2, (int64_t)1 << 40);
+        int stop = stop_if_short ? 1 : 0;
+        ull* cp = ctrl.get();
+        void* args[] = {(void*)&net, (void*)&cp, (void*)&max_phases, (void*)&stop};
+        LDS_CUDA(cudaLaunchCooperativeKernel((void*)hyper_flow_kernel, dim3(grid), dim3(FB), args, 0, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+    }
+    ull hc[HC_WORDS];
+    LDS_CUDA(cudaMemcpyAsync(hc, ctrl.get(), sizeof(hc), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    LDS_REQUIRE(hc[HC_STATUS] != 1, LDS_ETIMEOUT, "max flow: phase bound hit");
+    if (hc[HC_STATUS] == 2) return -1;
+    if (side && nv) LDS_LAUNCH(side_kernel, grid_for(nv, FB), FB, 0, s, h.get(), nv, side);
+    LDS_CUDA(cudaStreamSynchronize(s));
+    const ull ft = hc[HC_FLOW];
+    LDS_REQUIRE((int64_t)ft % K == 0, LDS_ECUDA, "max flow: flow value %llu is not a multiple of the scale", ft);
+    return (int64_t)ft / K;
+}
 
 int64_t pattern_max_flow(const int64_t* pptr, const int32_t* pidx, int32_t np, int32_t nv, int64_t p, int64_t q,
                          const int64_t* share, uint8_t* side, bool stop_if_short, cudaStream_t s) {
@@ -319,6 +644,10 @@ int64_t pattern_max_flow(const int64_t* pptr, const int32_t* pidx, int32_t np, i
         LDS_LAUNCH(split_kernel, grid_for(np, FB), FB, 0, s, pptr, np, share, qK, f.get(), big.get());
         n3 = exclusive_scan_i32_to_i64(big.get(), bigpos.get(), np + 1, s);
     }
+    // the vertex-node form is the default (variant 0)
+    const int variant = g_flow_variant.load(std::memory_order_relaxed);
+    if (variant != 1)
+        return hyper_max_flow(pptr, pidx, np, nv, nidx, f.get(), pK, K, side, stop_if_short, s);
     LDS_REQUIRE((int64_t)nv + n3 < (int64_t)DEAD, LDS_EOVERFLOW, "max flow: too many nodes");
     const int32_t nn = nv + (int32_t)n3;
     const int32_t nnp = std::max(nn, 1);
@@ -417,6 +746,13 @@ int64_t pattern_max_flow(const int64_t* pptr, const int32_t* pidx, int32_t np, i
 }  // namespace lds
 
 using namespace lds;
+
+extern "C" lds_status lds_set_flow_variant(int32_t variant) {
+    return guard([&] {
+        LDS_REQUIRE(variant >= 0 && variant <= 2, LDS_EINVAL, "lds_set_flow_variant: %d is not 0, 1 or 2", variant);
+        g_flow_variant.store(variant, std::memory_order_relaxed);
+    });
+}
 
 extern "C" lds_status lds_pattern_max_flow(int32_t nv, int32_t np, const int64_t* pat_ptr, const int32_t* pat_idx,
                                            int64_t p, int64_t q, int64_t* flow, uint8_t* source_side) {

@@ -206,6 +206,7 @@ struct Driver {
     int32_t N;
     lds_precision prec;
     bool include_zero;
+    lds_verify vmode;
     Bounds bG;
     Scratch sc;
     VerifyStats vst;
@@ -217,8 +218,8 @@ struct Driver {
     };
     std::vector<Found> found;
 
-    Driver(lds_graph* g, bool t, int32_t kk, int32_t n, lds_precision p, bool iz)
-        : G(g), tri(t), k(kk), N(n), prec(p), include_zero(iz), sc(g) {}
+    Driver(lds_graph* g, bool t, int32_t kk, int32_t n, lds_precision p, bool iz, lds_verify vm)
+        : G(g), tri(t), k(kk), N(n), prec(p), include_zero(iz), vmode(vm), sc(g) {}
 
     cudaStream_t st() const { return G->stream; }
 
@@ -300,7 +301,7 @@ struct Driver {
 
     void certify(const int32_t* comp, int32_t csize, int64_t npat) {
         if (npat == 0 && !include_zero) return;
-        bool ok = is_lds(G, tri, comp, csize, npat, bG, sc, &vst);
+        bool ok = is_lds(G, tri, comp, csize, npat, bG, sc, &vst, vmode);
         if (ok) {
             Found f;
             int64_t g = std::gcd(npat, (int64_t)csize);
@@ -616,16 +617,56 @@ thread_local lds_topk_stats_t t_last_stats{};
 
 extern "C" {
 
+static void topk_run(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, bool include_zero,
+                     lds_verify vmode, lds_result** out);
+
 lds_status lds_topk(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, lds_result** out) {
     return guard([&] {
         LDS_REQUIRE(g && out, LDS_EINVAL, "lds_topk: NULL argument");
+        topk_run(g, k, d, iters, p, false, LDS_VERIFY_BOUNDS, out);
+    });
+}
+
+lds_status lds_topk_ex(lds_graph* g, int32_t k, lds_density d, int32_t iters, const lds_options* opt,
+                       lds_result** out) {
+    return guard([&] {
+        LDS_REQUIRE(g && out, LDS_EINVAL, "lds_topk_ex: NULL argument");
+        lds_options o{LDS_EXACT, nullptr, 0, LDS_VERIFY_BOUNDS};
+        if (opt) o = *opt;
+        LDS_REQUIRE(o.verify == LDS_VERIFY_BOUNDS || o.verify == LDS_VERIFY_CORE || o.verify == LDS_VERIFY_WHOLE,
+                    LDS_EINVAL, "lds_topk_ex: bad verify value %d", (int)o.verify);
+        cudaStream_t cs = static_cast<cudaStream_t>(o.cuda_stream);
+        if (!cs || cs == g->stream) {
+            topk_run(g, k, d, iters, o.prec, o.include_zero_density != 0, o.verify, out);
+            return;
+        }
+        // the handle and its buffers follow the call's stream for the call, so that every
+        // stream-ordered free is ordered after the work that used the buffer
+        cudaStream_t own = g->stream;
+        LDS_CUDA(cudaStreamSynchronize(own));
+        set_stream(g, cs);
+        struct Back {
+            lds_graph* g;
+            cudaStream_t own, cs;
+            ~Back() {
+                cudaStreamSynchronize(cs);
+                set_stream(g, own);
+            }
+        } back{g, own, cs};
+        topk_run(g, k, d, iters, o.prec, o.include_zero_density != 0, o.verify, out);
+    });
+}
+
+static void topk_run(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_precision p, bool include_zero,
+                     lds_verify vmode, lds_result** out) {
+    {
         LDS_REQUIRE(k >= 1, LDS_EINVAL, "lds_topk: k = %d < 1", k);
         LDS_REQUIRE(d == LDS_EDGE || d == LDS_TRIANGLE, LDS_EINVAL, "lds_topk: bad density");
         LDS_REQUIRE(iters >= 1 && iters <= (d == LDS_EDGE ? 7000 : 3500), LDS_EINVAL,
                     "lds_topk: iters = %d out of range (refinement may run 8x iters)", iters);
         LDS_REQUIRE(p == LDS_EXACT || p == LDS_FP32 || p == LDS_FP64, LDS_EINVAL, "lds_topk: bad precision");
         *out = nullptr;
-        Driver drv(g, d == LDS_TRIANGLE, k, iters, p, false);
+        Driver drv(g, d == LDS_TRIANGLE, k, iters, p, include_zero, vmode);
         drv.run();
         // order: density descending, ties by smallest member id (original ids)
         struct R {
@@ -673,7 +714,7 @@ lds_status lds_topk(lds_graph* g, int32_t k, lds_density d, int32_t iters, lds_p
         }
         t_last_stats = drv.stats;
         *out = res;
-    });
+    }
 }
 
 void lds_result_free(lds_result* r) {

@@ -20,6 +20,8 @@
 // with a vertex in U and all three upper bounds >= rho, its vertices with
 // lb <= rho (Alg. 7).  Those vertices are reached by the edge search as well,
 // so U is the same edge-grown set.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <numeric>
 
@@ -128,98 +130,91 @@ __global__ void loop_fill_kernel(const int32_t* cnt, const int64_t* off, int32_t
         }
 }
 
-// triangles owned by their smallest member that is in the set (only those
-// with all vertices in the set when `all_in`), else for IsLTDS: triangles with a
-// member in the set and all ub >= rho, reduced to vertices with lb <= rho
-template <bool FILL>
-__global__ void tri_pat_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* vt_ptr,
-                               const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
-                               const uint8_t* in, const int32_t* local, bool all_in, const int64_t* un,
-                               const int64_t* ud, const int64_t* ln, const int64_t* ld, int64_t p, int64_t q,
-                               int32_t* cnt, int32_t* len, const int64_t* off, int64_t* pptr, int32_t* pidx,
-                               const int64_t* W, int64_t* share) {
+// ---- triangle patterns over the incidences of the set: one work item per
+// (member, incident triangle) pair, so that hubs with millions of triangles
+// are shared by the whole grid.  ioff is the exclusive prefix of the members'
+// triangle counts.  A triangle is taken by its smallest member in the set.
+
+__global__ void tri_inc_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* vt_ptr,
+                                     int32_t* icnt) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
-        int32_t c = 0, l = 0;
-        int64_t o = FILL ? off[i] : 0;
-        if (x < nact)
-            for (int64_t r = vt_ptr[x]; r < vt_ptr[x + 1]; ++r) {
-                int32_t t = vt_idx[r];
-                int32_t v[3] = {ta[t], tb[t], tc[t]};
-                // owner: smallest member in the set
-                int32_t owner = -1;
-                for (int j = 0; j < 3; ++j)
-                    if (in[v[j]] && (owner < 0 || v[j] < owner)) owner = v[j];
-                if (owner != x) continue;
-                if (all_in) {
-                    if (!(in[v[0]] && in[v[1]] && in[v[2]])) continue;
-                    if (FILL)
-                        for (int j = 0; j < 3; ++j) {
-                            pidx[3 * o + j] = local[v[j]];
-                            if (share) share[3 * o + j] = W[3 * (int64_t)t + j];
-                        }
-                    ++c;
-                    l += 3;
-                    ++o;
-                } else {
-                    bool valid = true;
-                    for (int j = 0; j < 3; ++j)
-                        if (lt_rho(un[v[j]], ud[v[j]], p, q)) valid = false;
-                    if (!valid) continue;
-                    // members with lb <= rho (all of them lie in U; the test on `in`
-                    // only guards the local index)
-                    int32_t mm = 0;
-                    for (int j = 0; j < 3; ++j)
-                        if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) ++mm;
-                    if (mm == 0) continue;
-                    if (FILL) {
-                        int64_t at = pptr[o];
-                        for (int j = 0; j < 3; ++j)
-                            if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) {
-                                if (share) share[at] = W[3 * (int64_t)t + j];
-                                pidx[at++] = local[v[j]];
-                            }
-                    }
-                    ++c;
-                    l += mm;
-                    ++o;
-                }
-            }
-        if (!FILL) {
-            cnt[i] = c;
-            len[i] = l;
-        }
+        const int32_t x = list[i];
+        icnt[i] = x < nact ? (int32_t)(vt_ptr[x + 1] - vt_ptr[x]) : 0;
     }
 }
 
-// length of every reduced triangle pattern, in the order tri_pat_kernel emits them
-__global__ void tri_len_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* vt_ptr, const int32_t* vt_idx,
-                               const int32_t* ta, const int32_t* tb, const int32_t* tc, const uint8_t* in,
-                               const int64_t* un, const int64_t* ud, const int64_t* ln, const int64_t* ld, int64_t p,
-                               int64_t q, const int64_t* off, int32_t* plen) {
+__device__ __forceinline__ int32_t tri_inc_member(const int64_t* ioff, int32_t k, int64_t item) {
+    int32_t lo = 0, hi = k;                  // last i with ioff[i] <= item
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (ioff[mid] <= item) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// members of triangle t that form its pattern (mask of columns), 0 when t is not
+// taken by x: all three in the set (all_in), else Alg. 7's reduction (all
+// ub >= rho; the members in the set with lb <= rho)
+__device__ __forceinline__ int tri_pattern_mask(int32_t x, int32_t t, const int32_t* ta, const int32_t* tb,
+                                                const int32_t* tc, const uint8_t* in, bool all_in,
+                                                const int64_t* un, const int64_t* ud, const int64_t* ln,
+                                                const int64_t* ld, int64_t p, int64_t q) {
+    const int32_t v[3] = {ta[t], tb[t], tc[t]};
+    int32_t owner = -1;
+    for (int j = 0; j < 3; ++j)
+        if (in[v[j]] && (owner < 0 || v[j] < owner)) owner = v[j];
+    if (owner != x) return 0;
+    if (all_in) return (in[v[0]] && in[v[1]] && in[v[2]]) ? 7 : 0;
+    for (int j = 0; j < 3; ++j)
+        if (lt_rho(un[v[j]], ud[v[j]], p, q)) return 0;
+    int mask = 0;
+    for (int j = 0; j < 3; ++j)
+        if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) mask |= 1 << j;
+    return mask;
+}
+
+// per item: 1 if it takes a pattern, and the pattern's length
+__global__ void tri_item_count_kernel(const int32_t* list, int32_t k, const int64_t* ioff, int64_t nitems,
+                                      const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta,
+                                      const int32_t* tb, const int32_t* tc, const uint8_t* in, bool all_in,
+                                      const int64_t* un, const int64_t* ud, const int64_t* ln, const int64_t* ld,
+                                      int64_t p, int64_t q, int32_t* take, int32_t* len) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
-        int64_t o = off[i];
-        if (x >= nact) continue;
-        for (int64_t r = vt_ptr[x]; r < vt_ptr[x + 1]; ++r) {
-            int32_t t = vt_idx[r];
-            int32_t v[3] = {ta[t], tb[t], tc[t]};
-            int32_t owner = -1;
-            for (int j = 0; j < 3; ++j)
-                if (in[v[j]] && (owner < 0 || v[j] < owner)) owner = v[j];
-            if (owner != x) continue;
-            bool valid = true;
-            for (int j = 0; j < 3; ++j)
-                if (lt_rho(un[v[j]], ud[v[j]], p, q)) valid = false;
-            if (!valid) continue;
-            int32_t mm = 0;
-            for (int j = 0; j < 3; ++j)
-                if (in[v[j]] && !gt_rho(ln[v[j]], ld[v[j]], p, q)) ++mm;
-            if (mm == 0) continue;
-            plen[o++] = mm;
-        }
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += stride) {
+        const int32_t i = tri_inc_member(ioff, k, it);
+        const int32_t x = list[i];
+        const int32_t t = vt_idx[vt_ptr[x] + (it - ioff[i])];
+        const int mask = tri_pattern_mask(x, t, ta, tb, tc, in, all_in, un, ud, ln, ld, p, q);
+        take[it] = mask != 0;
+        if (len) len[it] = __popc(mask);
+    }
+}
+
+// per taking item: its pattern's start (slot offset) and members, with the
+// Frank-Wolfe split of each member when share is given
+__global__ void tri_item_fill_kernel(const int32_t* list, int32_t k, const int64_t* ioff, int64_t nitems,
+                                     const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta,
+                                     const int32_t* tb, const int32_t* tc, const uint8_t* in, const int32_t* local,
+                                     bool all_in, const int64_t* un, const int64_t* ud, const int64_t* ln,
+                                     const int64_t* ld, int64_t p, int64_t q, const int64_t* patpos,
+                                     const int64_t* slotpos, int64_t* pptr, int32_t* pidx, const int64_t* W,
+                                     int64_t* share) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nitems; it += stride) {
+        const int32_t i = tri_inc_member(ioff, k, it);
+        const int32_t x = list[i];
+        const int32_t t = vt_idx[vt_ptr[x] + (it - ioff[i])];
+        const int mask = tri_pattern_mask(x, t, ta, tb, tc, in, all_in, un, ud, ln, ld, p, q);
+        if (!mask) continue;
+        const int32_t v[3] = {ta[t], tb[t], tc[t]};
+        int64_t at = slotpos ? slotpos[it] : 3 * patpos[it];
+        if (pptr) pptr[patpos[it]] = at;
+        for (int j = 0; j < 3; ++j)
+            if (mask & (1 << j)) {
+                if (share) share[at] = W[3 * (int64_t)t + j];
+                pidx[at++] = local[v[j]];
+            }
     }
 }
 
@@ -239,10 +234,11 @@ __global__ void narrow_u64_i32_kernel(const uint64_t* in, int64_t k, int32_t* ou
 }
 
 // one level of the search that grows U over neighbours with lb <= rho <= ub
+// (with use_lb = false: over neighbours with ub >= rho, the IsLDS-core search)
 __global__ void grow_level_kernel(const int32_t* frontier, int32_t fsize, int32_t nact, const int64_t* rowptr,
                                   const int32_t* col, uint8_t* inU, const int64_t* un, const int64_t* ud,
-                                  const int64_t* ln, const int64_t* ld, int64_t p, int64_t q, int32_t* next,
-                                  int32_t* nsize) {
+                                  const int64_t* ln, const int64_t* ld, int64_t p, int64_t q, bool use_lb,
+                                  int32_t* next, int32_t* nsize) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fsize; i += stride) {
         int32_t x = frontier[i];
@@ -250,7 +246,7 @@ __global__ void grow_level_kernel(const int32_t* frontier, int32_t fsize, int32_
         for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
             int32_t w = col[r];
             if (inU[w]) continue;
-            if (gt_rho(ln[w], ld[w], p, q)) continue;         // loop side, never joins U
+            if (use_lb && gt_rho(ln[w], ld[w], p, q)) continue;   // loop side, never joins U
             if (lt_rho(un[w], ud[w], p, q)) continue;         // phi(w) < rho
             unsigned int* word = (unsigned int*)(inU + (w & ~3));
             unsigned int bit = 1u << (8 * (w & 3));
@@ -275,6 +271,11 @@ __global__ void denser_neighbour_kernel(const int32_t* list, int32_t k, int32_t 
             }
         }
     }
+}
+
+__global__ void iota_i32_kernel(int32_t* out, int32_t n) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (int32_t)i;
 }
 
 __global__ void collect_kernel(const uint8_t* flag, int32_t n, int32_t* out, int32_t* cnt) {
@@ -310,22 +311,43 @@ __global__ void cc_init_kernel(const int32_t* list, int32_t k, int32_t* label) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) label[list[i]] = list[i];
 }
 
-__global__ void cc_step_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr, const int32_t* col,
-                               const uint8_t* in, int32_t* label, int32_t* changed) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
-        if (x >= nact) continue;
-        int32_t lx = __ldcg(label + x);
-        int32_t best = lx;
-        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-            int32_t w = col[r];
-            if (in[w]) best = min(best, __ldcg(label + w));
+// Every sweep of label propagation in one cooperative launch: each sweep lowers
+// every member's label to the smallest label among its in-set neighbours (atomic
+// minimum, so labels only fall), a grid barrier, and a stop when a sweep changed
+// nothing.  flags[0..1] alternate as the sweeps' change flags; flags[2] is set
+// when the sweep bound is hit.
+__global__ void cc_coop_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
+                               const int32_t* col, const uint8_t* in, int32_t* label, int32_t* flags,
+                               int64_t max_sweeps) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t sweep = 0;; ++sweep) {
+        if (sweep >= max_sweeps) {
+            if (tid == 0) flags[2] = 1;
+            return;
         }
-        if (best < lx) {
-            atomicMin(label + x, best);
-            *changed = 1;
+        int32_t* changed = flags + (sweep & 1);
+        for (int64_t i = tid; i < k; i += nthreads) {
+            const int32_t x = list[i];
+            if (x >= nact) continue;
+            const int32_t lx = __ldcg(label + x);
+            int32_t best = lx;
+            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+                const int32_t w = col[r];
+                if (in[w]) best = min(best, __ldcg(label + w));
+            }
+            if (best < lx) {
+                atomicMin(label + x, best);
+                *changed = 1;
+            }
         }
+        grid.sync();
+        const int32_t c = __ldcg(changed);
+        // the other flag is cleared for the next sweep; every thread has read this one
+        if (tid == 0) flags[(sweep + 1) & 1] = 0;
+        grid.sync();
+        if (!c) return;
     }
 }
 
@@ -464,36 +486,41 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
     const int64_t* ud = bb ? bb->ud.get() : nullptr;
     const int64_t* ln = bb ? bb->ln.get() : nullptr;
     const int64_t* ld = bb ? bb->ld.get() : nullptr;
-    if (k)
-        LDS_LAUNCH(tri_pat_kernel<false>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
-                   g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
-                   cnt.get(), len.get(), (const int64_t*)nullptr, (int64_t*)nullptr, (int32_t*)nullptr,
-                   (const int64_t*)nullptr, (int64_t*)nullptr);
-    int64_t np = scan_counts(cnt.get(), k, off, s);
-    DevBuf<int64_t> loffs;
-    int64_t nidx = scan_counts(len.get(), k, loffs, s);
-    pptr.alloc(np + 1, s);
-    pidx.alloc(std::max<int64_t>(nidx, 1), s);
-    if (warm) share->alloc(std::max<int64_t>(nidx, 1), s);
-    int64_t* sh = warm ? share->get() : nullptr;
-    if (all_in) {
-        LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(np + 1, VB), VB, 0, s, np, 3, pptr.get());
-    } else if (np) {
-        // pattern lengths are known only per owner; fill pattern starts with a pass that
-        // records each pattern's length, then scan
-        DevBuf<int32_t> plen(np + 1, s);
-        LDS_CUDA(cudaMemsetAsync(plen.get(), 0, (np + 1) * sizeof(int32_t), s));
-        LDS_LAUNCH(tri_len_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(),
-                   g->tb.get(), g->tc.get(), sc.in.get(), un, ud, ln, ld, p, q, off.get(), plen.get());
-        exclusive_scan_i32_to_i64(plen.get(), pptr.get(), np + 1, s);
+    {
+        // items = (member, incident triangle) pairs
+        DevBuf<int64_t> ioff;
+        if (k) LDS_LAUNCH(tri_inc_count_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), cnt.get());
+        const int64_t nitems = scan_counts(cnt.get(), k, ioff, s);
+        DevBuf<int32_t> take(nitems + 1, s), plen(all_in ? 0 : nitems + 1, s);
+        if (nitems)
+            LDS_LAUNCH(tri_item_count_kernel, grid_for(nitems, VB), VB, 0, s, list, k, ioff.get(), nitems,
+                       g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), all_in, un,
+                       ud, ln, ld, p, q, take.get(), all_in ? (int32_t*)nullptr : plen.get());
+        LDS_CUDA(cudaMemsetAsync(take.get() + nitems, 0, sizeof(int32_t), s));
+        DevBuf<int64_t> patpos(nitems + 1, s), slotpos;
+        const int64_t np = exclusive_scan_i32_to_i64(take.get(), patpos.get(), nitems + 1, s);
+        int64_t nidx = 3 * np;
+        if (!all_in) {
+            LDS_CUDA(cudaMemsetAsync(plen.get() + nitems, 0, sizeof(int32_t), s));
+            slotpos.alloc(nitems + 1, s);
+            nidx = exclusive_scan_i32_to_i64(plen.get(), slotpos.get(), nitems + 1, s);
+        }
+        pptr.alloc(np + 1, s);
+        pidx.alloc(std::max<int64_t>(nidx, 1), s);
+        if (warm) share->alloc(std::max<int64_t>(nidx, 1), s);
+        if (all_in) LDS_LAUNCH(uniform_pat_ptr_kernel, grid_for(np + 1, VB), VB, 0, s, np, 3, pptr.get());
+        else LDS_CUDA(cudaMemcpyAsync(pptr.get() + np, &nidx, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        if (nitems && np)
+            LDS_LAUNCH(tri_item_fill_kernel, grid_for(nitems, VB), VB, 0, s, list, k, ioff.get(), nitems,
+                       g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(),
+                       sc.local.get(), all_in, un, ud, ln, ld, p, q, patpos.get(),
+                       all_in ? (const int64_t*)nullptr : slotpos.get(), all_in ? (int64_t*)nullptr : pptr.get(),
+                       pidx.get(), warm ? (const int64_t*)g->fw_W.get() : (const int64_t*)nullptr,
+                       warm ? share->get() : (int64_t*)nullptr);
+        LDS_CUDA(cudaStreamSynchronize(s));      // nidx (host) is read by the copy above
+        if (n_main) *n_main = np;
+        return np;
     }
-    if (k && np)
-        LDS_LAUNCH(tri_pat_kernel<true>, grid_for(k, VB), VB, 0, s, list, k, nact, g->vt_ptr.get(), g->vt_idx.get(),
-                   g->ta.get(), g->tb.get(), g->tc.get(), sc.in.get(), sc.local.get(), all_in, un, ud, ln, ld, p, q,
-                   (int32_t*)nullptr, (int32_t*)nullptr, off.get(), all_in ? (int64_t*)nullptr : pptr.get(), pidx.get(),
-                   warm ? (const int64_t*)g->fw_W.get() : (const int64_t*)nullptr, sh);
-    if (n_main) *n_main = np;
-    return np;
 }
 
 int64_t build_all_patterns(lds_graph* h, bool tri, const int32_t* list, int32_t k, Scratch& sc,
@@ -531,42 +558,55 @@ bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch&
 }
 
 bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat, const Bounds& b, Scratch& sc,
-            VerifyStats* st) {
+            VerifyStats* st, lds_verify mode) {
     cudaStream_t s = g->stream;
     const int32_t n = g->n, nact = g->nact;
     int64_t gg = gcd64(npat, k);
     const int64_t p = npat / gg, q = k / gg;
     LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), (int32_t*)nullptr);
     DevBuf<int32_t> flag(1, s);
-    LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
-    LDS_LAUNCH(denser_neighbour_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
-               sc.in.get(), b.ln.get(), b.ld.get(), p, q, flag.get());
     int32_t hflag = 0;
-    LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    LDS_CUDA(cudaStreamSynchronize(s));
-    if (hflag) {
-        LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
-        if (st) ++st->denser_neighbour;
-        return false;
-    }
-    // grow U from S (sc.in2 marks U)
-    DevBuf<int32_t> fa(std::max(n, 1), s), fb(std::max(n, 1), s), cnt(1, s);
-    LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get(), (int32_t*)nullptr);
-    LDS_CUDA(cudaMemcpyAsync(fa.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    int32_t fsize = k, usize = k;
-    int32_t* cur = fa.get();
-    int32_t* nxt = fb.get();
-    DevBuf<int32_t> U(std::max(n, 1), s);
-    LDS_CUDA(cudaMemcpyAsync(U.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    while (fsize > 0) {
-        LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
-        LDS_LAUNCH(grow_level_kernel, grid_for(fsize, VB), VB, 0, s, cur, fsize, nact, g->rowptr.get(), g->col.get(),
-                   sc.in2.get(), b.un.get(), b.ud.get(), b.ln.get(), b.ld.get(), p, q, nxt, cnt.get());
-        LDS_CUDA(cudaMemcpyAsync(&fsize, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (mode == LDS_VERIFY_BOUNDS) {
+        LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
+        LDS_LAUNCH(denser_neighbour_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+                   sc.in.get(), b.ln.get(), b.ld.get(), p, q, flag.get());
+        LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
-        if (fsize) LDS_CUDA(cudaMemcpyAsync(U.get() + usize, nxt, fsize * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        usize += fsize;
-        std::swap(cur, nxt);
+        if (hflag) {
+            LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
+            if (st) ++st->denser_neighbour;
+            return false;
+        }
+    }
+    // grow U from S (sc.in2 marks U); the whole-graph baseline takes U = V
+    DevBuf<int32_t> fa(std::max(n, 1), s), fb(std::max(n, 1), s), cnt(1, s);
+    DevBuf<int32_t> U(std::max(n, 1), s);
+    int32_t usize = k;
+    if (mode == LDS_VERIFY_WHOLE) {
+        usize = n;
+        if (n) {
+            LDS_LAUNCH(iota_i32_kernel, grid_for(n, VB), VB, 0, s, U.get(), n);
+            LDS_LAUNCH(mark_kernel, grid_for(n, VB), VB, 0, s, U.get(), n, sc.in2.get(), (int32_t*)nullptr);
+        }
+    } else {
+        LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get(), (int32_t*)nullptr);
+        LDS_CUDA(cudaMemcpyAsync(fa.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        int32_t fsize = k;
+        int32_t* cur = fa.get();
+        int32_t* nxt = fb.get();
+        LDS_CUDA(cudaMemcpyAsync(U.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        while (fsize > 0) {
+            LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
+            LDS_LAUNCH(grow_level_kernel, grid_for(fsize, VB), VB, 0, s, cur, fsize, nact, g->rowptr.get(),
+                       g->col.get(), sc.in2.get(), b.un.get(), b.ud.get(), b.ln.get(), b.ld.get(), p, q,
+                       mode == LDS_VERIFY_BOUNDS, nxt, cnt.get());
+            LDS_CUDA(cudaMemcpyAsync(&fsize, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            if (fsize)
+                LDS_CUDA(cudaMemcpyAsync(U.get() + usize, nxt, fsize * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            usize += fsize;
+            std::swap(cur, nxt);
+        }
     }
     bool result;
     if (usize == k) {
@@ -582,9 +622,15 @@ bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat
         // patterns over U: swap marks so that sc.in marks U with local indices
         LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
         LDS_LAUNCH(mark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in.get(), sc.local.get());
+        // Alg. 4 / Alg. 7 networks (loops for denser outside neighbours, triangles reduced
+        // to members with lb <= rho); the core and whole-graph forms hold every vertex
+        // with ub >= rho that the search reaches (or all of V), so their patterns are
+        // those inside U and there are no loops
+        const bool bounds = mode == LDS_VERIFY_BOUNDS;
         DevBuf<int64_t> pptr, share;
         DevBuf<int32_t> pidx;
-        int64_t np = build_patterns(g, tri, U.get(), usize, sc, false, !tri, &b, p, q, pptr, pidx, nullptr, &share);
+        int64_t np = build_patterns(g, tri, U.get(), usize, sc, !bounds, bounds && !tri, &b, p, q, pptr, pidx, nullptr,
+                                    &share);
         DevBuf<uint8_t> side(usize, s);
         pattern_max_flow(pptr.get(), pidx.get(), (int32_t)np, usize, p, q, share.get(), side.get(), false, s);
         if (st) ++st->flows;
@@ -617,18 +663,32 @@ void components(lds_graph* g, const int32_t* list, int32_t k, Scratch& sc, DevBu
     starts.clear();
     members.alloc(std::max(k, 1), s);
     if (k == 0) return;
-    DevBuf<int32_t> label(std::max(g->n, 1), s), changed(1, s);
+    DevBuf<int32_t> label(std::max(g->n, 1), s), flags(3, s);
     LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get(), (int32_t*)nullptr);
     LDS_LAUNCH(cc_init_kernel, grid_for(k, VB), VB, 0, s, list, k, label.get());
-    for (int it = 0;; ++it) {
-        LDS_CUDA(cudaMemsetAsync(changed.get(), 0, sizeof(int32_t), s));
-        LDS_LAUNCH(cc_step_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
-                   sc.in.get(), label.get(), changed.get());
-        int32_t hc = 0;
-        LDS_CUDA(cudaMemcpyAsync(&hc, changed.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    {
+        // all sweeps in one cooperative launch
+        LDS_CUDA(cudaMemsetAsync(flags.get(), 0, 3 * sizeof(int32_t), s));
+        int per_sm = 0;
+        LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_coop_kernel, VB, 0));
+        LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "components: the sweep kernel cannot be resident");
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((k + VB - 1) / VB, (int64_t)num_sms() * per_sm));
+        const int32_t* lp = list;
+        int32_t kk = k, na = g->nact;
+        const int64_t* rp = g->rowptr.get();
+        const int32_t* cp = g->col.get();
+        const uint8_t* ip = sc.in.get();
+        int32_t* lab = label.get();
+        int32_t* fl = flags.get();
+        int64_t max_sweeps = (int64_t)k + 2;
+        void* args[] = {(void*)&lp, (void*)&kk, (void*)&na, (void*)&rp, (void*)&cp, (void*)&ip, (void*)&lab,
+                        (void*)&fl, (void*)&max_sweeps};
+        LDS_CUDA(cudaLaunchCooperativeKernel((void*)cc_coop_kernel, dim3(grid), dim3(VB), args, 0, s));
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        int32_t hf[3] = {0, 0, 0};
+        LDS_CUDA(cudaMemcpyAsync(hf, flags.get(), sizeof(hf), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
-        if (!hc) break;
-        LDS_REQUIRE(it <= k + 1, LDS_ETIMEOUT, "components: label propagation did not settle");
+        LDS_REQUIRE(hf[2] == 0, LDS_ETIMEOUT, "components: label propagation did not settle");
     }
     LDS_LAUNCH(unmark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in.get());
     const int bits = std::max(1, bit_length_u64((uint64_t)std::max(g->n, 1)));

@@ -29,8 +29,10 @@ struct VerifyStats {
 bool is_densest(lds_graph* g, bool tri, const int32_t* list, int32_t k, Scratch& sc, int64_t* npat);
 
 // IsLDS (edge) / IsLTDS (triangle) of the connected set `list` with |E(S)| (|T(S)|) = npat.
+// mode: the network of Alg. 4 / Alg. 7 (LDS_VERIFY_BOUNDS), the upper-bound-only
+// network of the Sec. 7 ablation (LDS_VERIFY_CORE), or the whole graph (LDS_VERIFY_WHOLE).
 bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat, const Bounds& b, Scratch& sc,
-            VerifyStats* st);
+            VerifyStats* st, lds_verify mode = LDS_VERIFY_BOUNDS);
 
 // Connected components of G[list]: members (device) grouped by component, each
 // component's members ascending, components ordered by smallest member;

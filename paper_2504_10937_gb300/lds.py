@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "LDS_OK", 1: "LDS_EINVAL", 2: "LDS_ENOMEM", 3: "LDS_ECUDA", 4
                 5: "LDS_EOVERFLOW", 6: "LDS_EBUSY"}
 DENSITY = {"edge": 0, "triangle": 1}
 PRECISION = {"exact": 0, "fp64": 1, "fp32": 2}
+VERIFY = {"bounds": 0, "core": 1, "whole": 2}
 MEM_HOST, MEM_DEVICE = 0, 1
 
 _lib = None
@@ -59,6 +60,11 @@ class TopkStats(ctypes.Structure):
 class Query(ctypes.Structure):
     _fields_ = [("g", ctypes.c_void_p), ("k", ctypes.c_int32), ("d", ctypes.c_int), ("iters", ctypes.c_int32),
                 ("p", ctypes.c_int)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("include_zero_density", ctypes.c_int32),
+                ("verify", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -101,10 +107,13 @@ def load():
     _sig(lib, "lds_debug_fail_alloc_after", None, [i32])
     _sig(lib, "lds_launch_count", i64, [])
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
+    _sig(lib, "lds_set_flow_variant", ctypes.c_int, [i32])
     _sig(lib, "lds_pattern_max_flow", ctypes.c_int, [i32, i32, P, P, i64, i64, ctypes.POINTER(i64), P])
     _sig(lib, "lds_prune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
     _sig(lib, "lds_topk", ctypes.c_int, [P, i32, ctypes.c_int, i32, ctypes.c_int,
                                          ctypes.POINTER(ctypes.POINTER(LdsResult))])
+    _sig(lib, "lds_topk_ex", ctypes.c_int, [P, i32, ctypes.c_int, i32, ctypes.POINTER(Options),
+                                            ctypes.POINTER(ctypes.POINTER(LdsResult))])
     _sig(lib, "lds_result_free", None, [ctypes.POINTER(LdsResult)])
     _sig(lib, "lds_topk_last_stats", ctypes.c_int, [ctypes.POINTER(TopkStats)])
     _sig(lib, "lds_extract_sg", ctypes.c_int, [P, P, ctypes.POINTER(i32), P, P, P, ctypes.POINTER(i64),
@@ -120,6 +129,7 @@ def load():
     _sig(lib, "lds_topk_batch", ctypes.c_int, [i32, ctypes.POINTER(Query), i32,
                                                ctypes.POINTER(ctypes.POINTER(LdsResult)), ctypes.POINTER(ctypes.c_int)])
     _sig(lib, "lds_batch_autotune", ctypes.c_int, [i32, ctypes.POINTER(Query), ctypes.POINTER(i32)])
+    _sig(lib, "lds_fw_batch_threads", i32, [i32])
     _sig(lib, "lds_debug_pick_next", i32, [i32, P, P, i64])
     _lib = lib
     return lib
@@ -157,6 +167,11 @@ def set_pass_profiling(on: bool):
 def set_fw_variant(variant: int):
     """0: automatic (degree-oriented pass when the keys fit); 1: symmetric-CSR pass."""
     _check(load().lds_set_fw_variant(int(variant)))
+
+
+def set_flow_variant(variant: int):
+    """0: automatic; 1: pattern-node push-relabel; 2: vertex-node phases."""
+    _check(load().lds_set_flow_variant(int(variant)))
 
 
 def launch_count() -> int:
@@ -231,6 +246,12 @@ def fw_batch(graphs, iters: int, precision: str = "exact") -> int:
     on = ctypes.c_int32()
     _check(load().lds_fw_batch(len(graphs), hs, int(iters), PRECISION[precision], ctypes.byref(on)))
     return int(on.value)
+
+
+def fw_batch_threads(nact: int) -> int:
+    """Threads per graph of the persistent batched FW launch for graphs of nact
+    active vertices (the autotuned choice of their size bucket, else 1024)."""
+    return int(load().lds_fw_batch_threads(int(nact)))
 
 
 def batch_autotune(queries) -> int:
@@ -409,12 +430,21 @@ class Graph:
         out["D"] = int(res.D)
         return out
 
-    def topk(self, k: int, density: str = "edge", iters: int = 100, precision: str = "exact"):
+    def topk(self, k: int, density: str = "edge", iters: int = 100, precision: str = "exact",
+             verify: str | None = None, include_zero: bool = False, stream: int | None = None):
         """Top-k LDSs (edge) or LTDSs (triangle): list of (Fraction density,
-        int32 array of member ids ascending), densest first."""
+        int32 array of member ids ascending), densest first.  With any of
+        verify ("bounds", "core", "whole"), include_zero or stream given, the
+        call goes through lds_topk_ex."""
         lib = load()
         res = ctypes.POINTER(LdsResult)()
-        _check(lib.lds_topk(self._h, int(k), DENSITY[density], int(iters), PRECISION[precision], ctypes.byref(res)))
+        if verify is None and not include_zero and stream is None:
+            _check(lib.lds_topk(self._h, int(k), DENSITY[density], int(iters), PRECISION[precision],
+                                ctypes.byref(res)))
+        else:
+            opt = Options(PRECISION[precision], stream, 1 if include_zero else 0, VERIFY[verify or "bounds"])
+            _check(lib.lds_topk_ex(self._h, int(k), DENSITY[density], int(iters), ctypes.byref(opt),
+                                   ctypes.byref(res)))
         try:
             return _result_list(res)
         finally:

@@ -113,8 +113,15 @@ def test_prune_fig1_example(lds):
     assert sorted(np.nonzero(st == 2)[0].tolist()) == parse_ids(exp["pruned_rule2"])
 
 
+@pytest.fixture(params=[1, 2], ids=["pattern_nodes", "vertex_nodes"])
+def flow_variant(lds, request):
+    lds.set_flow_variant(request.param)
+    yield request.param
+    lds.set_flow_variant(0)
+
+
 @pytest.mark.parametrize("seed", range(12))
-def test_pattern_max_flow_matches_dinic(lds, seed):
+def test_pattern_max_flow_matches_dinic(lds, seed, flow_variant):
     from oracle import verify as over
     rng = synth.SplitMix64(70000 + seed)
     nv = int(rng.integers(1, 40, 1)[0])
@@ -136,11 +143,30 @@ def test_pattern_max_flow_matches_dinic(lds, seed):
     assert [int(node[x] in side_want) for x in range(nv)] == side.tolist()
 
 
-def test_pattern_max_flow_larger_network(lds):
+def test_pattern_max_flow_larger_network(lds, flow_variant):
     from oracle import verify as over
     n, u, v, _ = synth.chung_lu(400, 2400, 2.1, seed=71, n_blocks=2, block_size_range=(20, 30))
     pats = list(zip(u.tolist(), v.tolist())) + [(x,) for x in range(0, n, 7)]
     for rho in (Fraction(3, 1), Fraction(7, 2), Fraction(11, 4)):
+        flow, side = lds.pattern_max_flow(n, pats, rho.numerator, rho.denominator)
+        net, s, t, node = over.pattern_network(range(n), pats, rho)
+        assert flow == net.max_flow(s, t)
+        sw = set(net.maximal_source_side(t))
+        assert [int(node[x] in sw) for x in range(n)] == side.tolist()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pattern_max_flow_triangle_network(lds, flow_variant, seed):
+    # the triangles of a graph with a dense block, at densities below, at and
+    # above the block's: saturated, tight and short networks
+    from oracle import verify as over
+    n, u, v, blocks = synth.gnp_planted(70, 0.08, (26,), (0.8,), seed=72 + seed)
+    tris = ograph.triangles(n, u, v)
+    pats = [tuple(t) for t in tris.tolist()] + [(x,) for x in range(0, n, 9)]
+    block = sorted(int(x) for x in blocks[0])
+    tb = len(ograph.induced_triangles(tris, block))
+    for rho in (Fraction(tb, len(block)), Fraction(tb, len(block)) - Fraction(1, 3), Fraction(2, 1),
+                Fraction(len(pats), n)):
         flow, side = lds.pattern_max_flow(n, pats, rho.numerator, rho.denominator)
         net, s, t, node = over.pattern_network(range(n), pats, rho)
         assert flow == net.max_flow(s, t)
@@ -164,6 +190,58 @@ def test_topk_matches_definition_small(lds, seed, triangle):
             for N, prec in ((3, "exact"), (40, "fp32"), (25, "fp64")):
                 got = _as_lists(g.topk(k, dens, N, prec))
                 assert got == truth[:k], (k, N, prec)
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("triangle", [False, True])
+def test_topk_verification_ablation_same_sets(lds, seed, triangle):
+    # Sec. 7's verification ablation: the upper-bound-only networks (IsLDS-core,
+    # IsLTDS-core) and the whole-graph baseline certify exactly the sets that
+    # Alg. 4 / Alg. 7 certify, which are the definition's (brute force)
+    from oracle import brute
+    n, u, v = synth.gnp_planted(10 + seed % 3, 0.3 + 0.04 * (seed % 5), seed=12000 + seed)[:3]
+    truth = brute.brute_lds(n, u, v, triangle=triangle)
+    dens = "triangle" if triangle else "edge"
+    with lds.Graph(n, u, v) as g:
+        for mode in ("bounds", "core", "whole"):
+            for k in (1, 5):
+                assert _as_lists(g.topk(k, dens, 30, "exact", verify=mode)) == truth[:k], (mode, k)
+
+
+def test_topk_verification_ablation_medium(lds):
+    from oracle import decomp
+    n, u, v, _ = synth.gnp_planted(300, 0.012, (12, 10, 9, 8), (0.9, 0.85, 0.8, 0.9), seed=11007)
+    truth = decomp.lds_exact(n, u, v)
+    truth_t = decomp.ltds_exact(n, u, v, ograph.triangles(n, u, v))
+    with lds.Graph(n, u, v) as g:
+        for mode in ("core", "whole"):
+            assert _as_lists(g.topk(4, "edge", 100, verify=mode)) == [(d, c) for d, c in truth[:4]], mode
+            assert _as_lists(g.topk(3, "triangle", 100, verify=mode)) == [(d, c) for d, c in truth_t[:3]], mode
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("triangle", [False, True])
+def test_topk_include_zero_density(lds, seed, triangle):
+    # Def. 3 / Def. 9 make isolated vertices (triangle-free connected sets) LDSs
+    # (LTDSs) of density 0; with include_zero_density they count as results
+    from oracle import brute
+    n, u, v = synth.gnp_planted(11, 0.14 + 0.03 * (seed % 3), seed=13000 + seed)[:3]
+    truth = brute.brute_lds(n, u, v, triangle=triangle, include_zero=True)
+    dens = "triangle" if triangle else "edge"
+    with lds.Graph(n, u, v) as g:
+        got = _as_lists(g.topk(len(truth) + 2, dens, 30, "exact", include_zero=True))
+    assert got == truth
+
+
+def test_topk_ex_on_a_caller_stream(lds):
+    import torch
+    n, u, v, _ = synth.gnp_planted(300, 0.012, (12, 10), (0.9, 0.85), seed=11009)
+    s = torch.cuda.Stream()
+    with lds.Graph(n, u, v) as g:
+        want = _as_lists(g.topk(3, "edge", 100))
+        got = _as_lists(g.topk(3, "edge", 100, stream=s.cuda_stream))
+        again = _as_lists(g.topk(3, "edge", 100))
+    assert got == want and again == want
 
 
 def test_topk_fig1(lds):
