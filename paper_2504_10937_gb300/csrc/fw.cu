@@ -578,8 +578,12 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
         bool fast = g_fw_variant != 1 && run_edge_fw_oriented(g, iters, p, true, want_last, fo, timer);
         if (fast) {
             LDS_CUDA(cudaEventRecord(e1, s));
+            const std::string pk(g->pass_kernel);
             g->pass_bytes = 4 * g->m + 8 * ((g->m + 31) / 32) + 4 * g->fwv_nz +
-                            (std::string(g->pass_kernel) == "fw_opass32_kernel" ? 4 : 8) * (int64_t)nact;
+                            (pk == "fw_opass32_kernel" || pk == "fw_coop32_kernel" ? 4 : 8) * (int64_t)nact;
+            // the cooperative kernel also runs the vertex update: words and counts read and
+            // written, row ranges read, the plane read again
+            if (pk == "fw_coop32_kernel") g->pass_bytes += 20 * (int64_t)nact + 4 * ((g->m + 31) / 32);
             R_int = std::move(fo.R_int);
             r_int = std::move(fo.r_int);
             g->fw_W = std::move(fo.W_edge);
@@ -650,8 +654,9 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
     float ms = 0;
     LDS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     g->fw_ms = ms;
-    g->pass_launches = timer.used / 2;
-    g->pass_us = timer.used ? 1000.0 * timer.total_ms() / (timer.used / 2) : 0.0;
+    // per iteration: a cooperative launch covers many iterations
+    g->pass_launches = timer.iters;
+    g->pass_us = timer.iters ? 1000.0 * timer.total_ms() / (double)timer.iters : 0.0;
     g->fw_valid = true;
     g->fw_density = d;
     g->fw_prec = p;
@@ -739,7 +744,7 @@ void lds_set_pass_profiling(int32_t on) { g_pass_profiling = on != 0; }
 
 lds_status lds_set_fw_variant(int32_t variant) {
     return guard([&] {
-        LDS_REQUIRE(variant >= 0 && variant <= 2, LDS_EINVAL, "lds_set_fw_variant: variant must be 0, 1 or 2");
+        LDS_REQUIRE(variant >= 0 && variant <= 4, LDS_EINVAL, "lds_set_fw_variant: variant must be 0 to 4");
         g_fw_variant = variant;
     });
 }

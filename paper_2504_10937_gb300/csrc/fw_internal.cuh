@@ -24,10 +24,12 @@ struct PassTimer {
         }
         LDS_CUDA(cudaEventRecord(ev[used], s));
     }
-    void stop(cudaStream_t s) {
+    int64_t iters = 0;     // iterations the timed launches covered (one per launch unless given)
+    void stop(cudaStream_t s, int64_t covered = 1) {
         if (!on) return;
         LDS_CUDA(cudaEventRecord(ev[used + 1], s));
         used += 2;
+        iters += covered;
     }
     double total_ms() {
         double t = 0;

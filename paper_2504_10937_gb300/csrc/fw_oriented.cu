@@ -18,7 +18,10 @@
 // count is the popcount of its lanes (one atomic per row segment); the
 // target's count goes to shared memory for hot targets (flushed once per
 // block) and to a global atomic otherwise.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <type_traits>
 
 #include "fw_internal.cuh"
 #include "prims.cuh"
@@ -86,9 +89,21 @@ __global__ void nz_rows_kernel(const uint64_t* key, const int32_t* start, const 
     }
 }
 
+// slots per row (rows are the fw ids of the lower-ranked endpoints)
+__global__ void row_count_kernel(const uint64_t* key, int64_t m, int64_t nact, int32_t* cnt) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += stride)
+        atomicAdd(cnt + (int64_t)(key[s] / (uint64_t)nact), 1);
+}
+
 __global__ void widen_eid_kernel(const uint32_t* in, int64_t m, int64_t* out) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) out[i] = in[i];
+}
+
+__global__ void narrow_i64_i32_kernel(const int64_t* in, int64_t k, int32_t* out) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (int32_t)in[i];
 }
 
 // ---------------------------------------------------------------- iteration kernels
@@ -209,22 +224,23 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
 constexpr int HOT32 = 32768;
 constexpr size_t OP32_SMEM = (size_t)HOT32 * 4 + (size_t)HOT32 * 2;
 
-template <int U, class Word>
-__global__ void __launch_bounds__(OP_THREADS, 1)
-    fw_opass32_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
-                      const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks,
-                      const Word* __restrict__ word, const int32_t* __restrict__ perm, int32_t nhot,
-                      int32_t* __restrict__ cnt, uint32_t* __restrict__ plane) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    Word* hword = reinterpret_cast<Word*>(smem);
-    uint32_t* hcnt2 = reinterpret_cast<uint32_t*>(smem + (size_t)HOT32 * 4);   // two 16-bit counters per word
+// One pass over every stored slot.  ROWS: the row endpoints' counts are left
+// out of the pass; the vertex update takes them as popcounts of each row's bit
+// range in this iteration's plane.  COOP: the body runs inside a cooperative
+// kernel whose other blocks rewrite the load words between passes, so words
+// are read through L2 (never the read-only data path).
+template <int U, class Word, bool ROWS, bool COOP>
+__device__ __forceinline__ void opass32_body(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
+                                             const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks,
+                                             const Word* word, const int32_t* __restrict__ perm, int32_t nhot,
+                                             int32_t* cnt, uint32_t* plane, Word* hword, uint32_t* hcnt2) {
     {
         const uint4* w4 = reinterpret_cast<const uint4*>(word);
         uint4* h4 = reinterpret_cast<uint4*>(hword);
         const int n4 = nhot >> 2;
 #pragma unroll 8
-        for (int i = threadIdx.x; i < n4; i += blockDim.x) h4[i] = __ldg(w4 + i);
-        for (int i = (n4 << 2) + threadIdx.x; i < nhot; i += blockDim.x) hword[i] = __ldg(word + i);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) h4[i] = COOP ? __ldcg(w4 + i) : __ldg(w4 + i);
+        for (int i = (n4 << 2) + threadIdx.x; i < nhot; i += blockDim.x) hword[i] = COOP ? __ldcg(word + i) : __ldg(word + i);
         uint4* c4 = reinterpret_cast<uint4*>(hcnt2);
         for (int i = threadIdx.x; i < (nhot + 7) >> 3; i += blockDim.x) c4[i] = make_uint4(0, 0, 0, 0);
     }
@@ -281,7 +297,7 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
             if (valid[k] && ws[k] == wt[k]) srecv = __ldg(perm + src[k]) > __ldg(perm + tgt[k]);
             const uint32_t bal = __ballot_sync(FULL, srecv);
             if (lane == 0 && g < nch) plane[g] = bal;
-            if (valid[k] && (lane == 0 || ((f[k] >> lane) & 1u))) {
+            if (!ROWS && valid[k] && (lane == 0 || ((f[k] >> lane) & 1u))) {
                 const uint32_t above = f[k] & ~le;
                 const uint32_t below_end = above ? ((above & (0u - above)) - 1u) : FULL;
                 const int cs = __popc(bal & ge & below_end);
@@ -291,8 +307,16 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
                 }
             }
             if (valid[k] && !srecv) {
-                if (tgt[k] < nhot) atomicAdd(hcnt2 + (tgt[k] >> 1), 1u << ((tgt[k] & 1) << 4));
-                else atomicAdd(cnt + tgt[k], 1);
+                if (ROWS) {
+                    // one generic atomic: a packed shared counter for a hot target, else its global one
+                    const bool hot = tgt[k] < nhot;
+                    uint32_t* pc = hot ? hcnt2 + (tgt[k] >> 1) : reinterpret_cast<uint32_t*>(cnt + tgt[k]);
+                    atomicAdd(pc, hot ? 1u << ((tgt[k] & 1) << 4) : 1u);
+                } else if (tgt[k] < nhot) {
+                    atomicAdd(hcnt2 + (tgt[k] >> 1), 1u << ((tgt[k] & 1) << 4));
+                } else {
+                    atomicAdd(cnt + tgt[k], 1);
+                }
             }
         }
     }
@@ -304,6 +328,19 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
             if (v >> 16) atomicAdd(cnt + 2 * i + 1, (int)(v >> 16));
         }
     }
+}
+
+template <int U, class Word, bool ROWS>
+__global__ void __launch_bounds__(OP_THREADS, 1)
+    fw_opass32_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
+                      const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks,
+                      const Word* __restrict__ word, const int32_t* __restrict__ perm, int32_t nhot,
+                      int32_t* __restrict__ cnt, uint32_t* __restrict__ plane) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Word* hword = reinterpret_cast<Word*>(smem);
+    uint32_t* hcnt2 = reinterpret_cast<uint32_t*>(smem + (size_t)HOT32 * 4);   // two 16-bit counters per word
+    opass32_body<U, Word, ROWS, false>(col, chunk_nz0, nzrow, nslots, nchunks, word, perm, nhot, cnt, plane, hword,
+                                       hcnt2);
 }
 
 __global__ void oword_init_kernel(const int64_t* rowptr, const int32_t* perm, int32_t nact, bool fp32, uint32_t* w32,
@@ -325,6 +362,98 @@ __global__ void oword_update_exact_kernel(uint32_t* __restrict__ w, int32_t* __r
             w[p] += inc * (uint32_t)c;
             cnt[p] = 0;
         }
+    }
+}
+
+// receipts of fw id p as a row endpoint in this iteration: the set bits of the
+// plane over its row's slots [a, b)
+__device__ __forceinline__ int32_t row_receipts(const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ plane,
+                                                int64_t p) {
+    const int32_t a = rowptr[p], b = rowptr[p + 1];
+    int32_t c = 0;
+    if (a < b) {
+        const int32_t wa = a >> 5, wb = (b - 1) >> 5;
+        for (int32_t q = wa; q <= wb; ++q) {
+            uint32_t bits = plane[q];
+            if (q == wa) bits &= FULL << (a & 31);
+            if (q == wb) bits &= lanes_le((b - 1) & 31);
+            c += __popc(bits);
+        }
+    }
+    return c;
+}
+
+__global__ void oword_update_rows_exact_kernel(uint32_t* __restrict__ w, int32_t* __restrict__ cnt,
+                                               const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ plane,
+                                               int32_t nact, uint32_t inc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += stride) {
+        const int32_t t = cnt[p];
+        const int32_t c = t + row_receipts(rowptr, plane, p);
+        if (c) w[p] += inc * (uint32_t)c;
+        if (t) cnt[p] = 0;
+    }
+}
+
+__global__ void oword_update_rows_fp32_kernel(float* __restrict__ r32, int32_t* __restrict__ cnt,
+                                              const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ plane,
+                                              int32_t nact, float gam, float one_minus) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nact; p += stride) {
+        const int32_t t = cnt[p];
+        const int32_t c = t + row_receipts(rowptr, plane, p);
+        r32[p] = __fadd_rn(__fmul_rn(one_minus, r32[p]), __fmul_rn(gam, (float)c));
+        if (t) cnt[p] = 0;
+    }
+}
+
+// Iterations i_first .. i_first + K - 1 in one cooperative launch: each runs
+// the pass (targets' receipts; choice plane it of `planes`), a grid barrier,
+// the vertex update (row endpoints' receipts from the plane, then R += 2(i+1) c
+// for the exact words or r <- (1 - gamma) r + gamma c in binary32 with gamma =
+// fl(2 / (i + 2))), and a second barrier before the next pass stages the new
+// words.  Same iterates, ties and rounding as the per-iteration launches.
+template <class Word>
+__global__ void __launch_bounds__(OP_THREADS, 1)
+    fw_coop32_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
+                     const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks, Word* word,
+                     const int32_t* __restrict__ perm, int32_t nhot, int32_t* cnt, const int32_t* __restrict__ rowptr,
+                     uint32_t* planes, int32_t nact, int32_t i_first, int32_t K) {
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    extern __shared__ __align__(16) unsigned char smem[];
+    Word* hword = reinterpret_cast<Word*>(smem);
+    uint32_t* hcnt2 = reinterpret_cast<uint32_t*>(smem + (size_t)HOT32 * 4);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int32_t it = 0; it < K; ++it) {
+        const int32_t i = i_first + it;
+        uint32_t* plane = planes + (int64_t)it * nchunks;
+        opass32_body<OP_UNROLL, Word, true, true>(col, chunk_nz0, nzrow, nslots, nchunks, word, perm, nhot, cnt, plane,
+                                                  hword, hcnt2);
+        grid.sync();
+        for (int64_t p = tid; p < nact; p += nthreads) {
+            const int32_t t = __ldcg(cnt + p);
+            int32_t c = t;
+            const int32_t a = rowptr[p], b = rowptr[p + 1];
+            if (a < b) {
+                const int32_t wa = a >> 5, wb = (b - 1) >> 5;
+                for (int32_t q = wa; q <= wb; ++q) {
+                    uint32_t bits = __ldcg(plane + q);
+                    if (q == wa) bits &= FULL << (a & 31);
+                    if (q == wb) bits &= lanes_le((b - 1) & 31);
+                    c += __popc(bits);
+                }
+            }
+            if constexpr (std::is_same<Word, float>::value) {
+                const float gam = __fdiv_rn(2.0f, (float)(i + 2));
+                const float om = __fsub_rn(1.0f, gam);
+                word[p] = __fadd_rn(__fmul_rn(om, word[p]), __fmul_rn(gam, (float)c));
+            } else {
+                if (c) word[p] += (uint32_t)(2 * (i + 1)) * (uint32_t)c;
+            }
+            if (t) cnt[p] = 0;
+        }
+        grid.sync();
     }
 }
 
@@ -506,6 +635,17 @@ void ensure_fw_view(lds_graph* g) {
         LDS_LAUNCH(nz_rows_kernel, grid_for(m, blk), blk, 0, s, key.get(), start.get(), rexcl.get(), m, (int64_t)nact,
                    g->fwv_nzrow.get(), g->fwv_chunk_nz0.get());
         LDS_LAUNCH(widen_eid_kernel, grid_for(m, blk), blk, 0, s, eid.get(), m, g->fwv_edge.get());
+        DevBuf<int32_t> rc(nact + 1, s);
+        DevBuf<int64_t> rp64(nact + 1, s);
+        LDS_CUDA(cudaMemsetAsync(rc.get(), 0, (nact + 1) * sizeof(int32_t), s));
+        LDS_LAUNCH(row_count_kernel, grid_for(m, blk), blk, 0, s, key.get(), m, (int64_t)nact, rc.get());
+        exclusive_scan_i32_to_i64(rc.get(), rp64.get(), (int64_t)nact + 1, s);
+        g->fwv_rowptr.alloc(nact + 1, s);
+        LDS_LAUNCH(narrow_i64_i32_kernel, grid_for(nact + 1, blk), blk, 0, s, rp64.get(), (int64_t)nact + 1,
+                   g->fwv_rowptr.get());
+    } else {
+        g->fwv_rowptr.alloc(std::max(nact, 0) + 1, s);
+        LDS_CUDA(cudaMemsetAsync(g->fwv_rowptr.get(), 0, (std::max(nact, 0) + 1) * sizeof(int32_t), s));
     }
     LDS_CUDA(cudaStreamSynchronize(s));
     g->fwv_built = true;
@@ -550,6 +690,11 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
     const int64_t Dn = (int64_t)(N + 1) * (N + 2);
     // 32-bit words: every scaled load below 2^32 and per-block hot counts below 2^16
     extern int g_fw_variant;
+    // variant 3 keeps the row endpoints' counts inside the pass; variant 4 counts them
+    // in the vertex update but launches pass and update once per iteration; the
+    // default runs many iterations per cooperative launch
+    const bool rows = g_fw_variant != 3;
+    const bool coop = g_fw_variant == 0;
     bool use32 = g_fw_variant != 2 && maxdeg < 65536 && (p == LDS_FP32 || (unsigned __int128)maxdeg * (unsigned __int128)Dn < ((unsigned __int128)1 << 32));
     if (!use32) {
         if (p == LDS_EXACT) {
@@ -582,12 +727,18 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
         if (nact)
             LDS_LAUNCH(oword_init_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), g->fwv_perm.get(), nact, fp32,
                        w32.get(), r32.get());
-        if (fp32)
-            LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, float>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
-        else
-            LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, uint32_t>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_coop32_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_coop32_kernel<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, float, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, uint32_t, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, float, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
+        LDS_CUDA(cudaFuncSetAttribute(fw_opass32_kernel<OP_UNROLL, uint32_t, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OP32_SMEM));
         g->pass_kernel = "fw_opass32_kernel";
     } else {
         nhot = std::min(nact, HOT);
@@ -601,25 +752,83 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
     int stored = 0;
     int64_t first_i = 1;
     int64_t last_plane = 0;
-    for (int i = 1; i <= N; ++i) {
+    if (use32 && coop && nchunks) {
+        int per_sm = 0;
+        if (fp32) LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_coop32_kernel<float>, OP_THREADS,
+                                                                         OP32_SMEM));
+        else LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_coop32_kernel<uint32_t>, OP_THREADS,
+                                                                    OP32_SMEM));
+        LDS_REQUIRE(per_sm >= 1, LDS_ECUDA, "fw: the cooperative pass cannot be resident");
+        g->pass_kernel = "fw_coop32_kernel";
+        int i = 1;
+        while (i <= N) {
+            int32_t kk = std::min(K - stored, N - i + 1);
+            uint32_t* pl = planes.get() + (int64_t)stored * nchunks;
+            const int32_t* pcol = g->fwv_col.get();
+            const int32_t* pz = g->fwv_chunk_nz0.get();
+            const int32_t* pnz = g->fwv_nzrow.get();
+            const int32_t* pperm = g->fwv_perm.get();
+            const int32_t* prow = g->fwv_rowptr.get();
+            int32_t* pcnt = cnt.get();
+            int64_t nsl = m, nch = nchunks;
+            int32_t nh = nhot, na = nact, i0 = i;
+            void* wp = fp32 ? (void*)r32.get() : (void*)w32.get();
+            void* args[] = {(void*)&pcol, (void*)&pz, (void*)&pnz, (void*)&nsl, (void*)&nch, (void*)&wp, (void*)&pperm,
+                            (void*)&nh, (void*)&pcnt, (void*)&prow, (void*)&pl, (void*)&na, (void*)&i0, (void*)&kk};
+            timer.start(s);
+            if (fp32)
+                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<float>, dim3(grid), dim3(OP_THREADS), args,
+                                                     OP32_SMEM, s));
+            else
+                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<uint32_t>, dim3(grid), dim3(OP_THREADS),
+                                                     args, OP32_SMEM, s));
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+            timer.stop(s, kk);
+            stored += kk;
+            i += kk;
+            if (stored == K || i > N) {
+                fold_planes(planes.get(), stored, nchunks, m, first_i, 2, W.get(), s);
+                last_plane = stored - 1;
+                if (i <= N) {
+                    stored = 0;
+                    first_i = i;
+                }
+            }
+        }
+    }
+    for (int i = (use32 && coop && nchunks) ? N + 1 : 1; i <= N; ++i) {
         uint32_t* plane = planes.get() + (int64_t)stored * nchunks;
         if (nchunks) {
             const float gam = 2.0f / (float)(i + 2);
             const float om = 1.0f - gam;
             timer.start(s);
-            if (use32 && fp32)
-                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, float>), grid, OP_THREADS, OP32_SMEM, s, g->fwv_col.get(),
-                           g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, r32.get(), g->fwv_perm.get(), nhot,
-                           cnt.get(), plane);
+            if (use32 && rows && fp32)
+                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, float, true>), grid, OP_THREADS, OP32_SMEM, s,
+                           g->fwv_col.get(), g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, r32.get(),
+                           g->fwv_perm.get(), nhot, cnt.get(), plane);
+            else if (use32 && rows)
+                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, uint32_t, true>), grid, OP_THREADS, OP32_SMEM, s,
+                           g->fwv_col.get(), g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, w32.get(),
+                           g->fwv_perm.get(), nhot, cnt.get(), plane);
+            else if (use32 && fp32)
+                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, float, false>), grid, OP_THREADS, OP32_SMEM, s,
+                           g->fwv_col.get(), g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, r32.get(),
+                           g->fwv_perm.get(), nhot, cnt.get(), plane);
             else if (use32)
-                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, uint32_t>), grid, OP_THREADS, OP32_SMEM, s, g->fwv_col.get(),
-                           g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, w32.get(), g->fwv_perm.get(), nhot,
-                           cnt.get(), plane);
+                LDS_LAUNCH((fw_opass32_kernel<OP_UNROLL, uint32_t, false>), grid, OP_THREADS, OP32_SMEM, s,
+                           g->fwv_col.get(), g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, w32.get(),
+                           g->fwv_perm.get(), nhot, cnt.get(), plane);
             else
                 LDS_LAUNCH(fw_opass_kernel<OP_UNROLL>, grid, OP_THREADS, OP_SMEM, s, g->fwv_col.get(),
                            g->fwv_chunk_nz0.get(), g->fwv_nzrow.get(), m, nchunks, key.get(), nhot, cnt.get(), plane);
             timer.stop(s);
-            if (use32 && fp32)
+            if (use32 && rows && fp32)
+                LDS_LAUNCH(oword_update_rows_fp32_kernel, grid_for(nact, blk), blk, 0, s, r32.get(), cnt.get(),
+                           g->fwv_rowptr.get(), plane, nact, gam, om);
+            else if (use32 && rows)
+                LDS_LAUNCH(oword_update_rows_exact_kernel, grid_for(nact, blk), blk, 0, s, w32.get(), cnt.get(),
+                           g->fwv_rowptr.get(), plane, nact, (uint32_t)(2 * (i + 1)));
+            else if (use32 && fp32)
                 LDS_LAUNCH(oword_update_fp32_kernel, grid_for(nact, blk), blk, 0, s, r32.get(), cnt.get(), nact, gam, om);
             else if (use32)
                 LDS_LAUNCH(oword_update_exact_kernel, grid_for(nact, blk), blk, 0, s, w32.get(), cnt.get(), nact,

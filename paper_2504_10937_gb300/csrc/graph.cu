@@ -369,6 +369,7 @@ void set_stream(lds_graph* g, cudaStream_t s) {
     g->fwv_nzrow.s = s;
     g->fwv_chunk_nz0.s = s;
     g->fwv_edge.s = s;
+    g->fwv_rowptr.s = s;
     g->fwv_ta.s = s;
     g->fwv_tb.s = s;
     g->fwv_tc.s = s;

@@ -44,6 +44,7 @@ struct lds_graph {
     lds::DevBuf<int32_t> fwv_nzrow;    // [fwv_nz] fw id of each non-empty row, ascending
     lds::DevBuf<int32_t> fwv_chunk_nz0;// [ceil(m / 32)] non-empty-row index of slot 32 g
     lds::DevBuf<int64_t> fwv_edge;     // [m] canonical edge id of each slot
+    lds::DevBuf<int32_t> fwv_rowptr;   // [nact + 1] slots of the row of fw id p: rowptr[p] .. rowptr[p+1]
     lds::DevBuf<int32_t> fwv_ta, fwv_tb, fwv_tc;  // triangles in fw ids (lazy)
 
     // state of the most recent Frank-Wolfe run (internal ids), read by the later stages
@@ -99,5 +100,10 @@ void map_ids(const int32_t* in, const int32_t* map, int64_t k, int32_t* out, cud
 // Scatter a per-internal-vertex array to original ids: out[to_orig[i]] = in[i].
 void to_original_order_i64(const lds_graph* g, const int64_t* in_int, int64_t* out_orig);
 void to_original_order_f64(const lds_graph* g, const double* in_int, double* out_orig);
+
+// Batched on-chip Frank-Wolfe (fw_batch.cu): tunes the threads per graph of every
+// size bucket among the given graphs (kept for the process), and reports the choice.
+void fw_batch_autotune(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p);
+int32_t fw_batch_threads(int32_t nact);
 
 }  // namespace lds

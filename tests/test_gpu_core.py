@@ -84,7 +84,7 @@ def test_degenerate_graphs(lds):
             assert g.triangles().shape == (0, 3)
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["oriented32", "symmetric", "oriented64"])
+@pytest.fixture(params=[0, 1, 2, 3, 4], ids=["oriented32_coop", "symmetric", "oriented64", "oriented32", "oriented32_rows"])
 def variant(request, lds):
     lds.set_fw_variant(request.param)
     yield request.param
