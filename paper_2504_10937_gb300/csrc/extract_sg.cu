@@ -16,10 +16,11 @@
 //    to its lowest-load S vertex; for an edge that is "all weight to the other
 //    endpoint".  S is accepted when every X vertex stays above max_S r' and
 //    every Z vertex below min_S r'; a failed candidate merges with the next one
-//    (Alg. 2's loop).  Each check is vertex-centric: the segment's vertices walk
-//    their edges (triangles), the S-side changes go to a per-position array and
-//    the outside changes become (segment, vertex) records that are sorted and
-//    summed.  The first round checks every candidate at once; a failure is
+//    (Alg. 2's loop).  Each check walks the incidences (edges, triangles) of
+//    the segment's vertices, one work item per incidence so that hubs are
+//    shared by the whole grid; the S-side changes go to a per-position array
+//    and the outside changes become (segment, vertex) records that are sorted
+//    and summed.  The first round checks every candidate at once; a failure is
 //    followed by single checks of the growing merged segment.
 // 5. Accepted groups give lo = min_S R', hi = max_S R' (over the denominator D);
 //    by Lemma 4 / Lemma 8 lo <= D phi(u) <= hi for u in the group.
@@ -186,118 +187,233 @@ __global__ void seg_of_pos_kernel(const int64_t* sa, const int64_t* sb, int32_t 
     }
 }
 
-// Records are written in two passes: the first stores the number of records
-// of every position (cnt), the second writes them from that position's offset
-// (off, the exclusive scan of cnt), so no counter is shared.
-struct Rec {
-    uint64_t* key;
-    int64_t* val;
-    int64_t* cnt;          // [positions] count pass
-    const int64_t* off;    // [positions] fill pass
-};
+// ---- checks spread over incidences: every (position, incident edge or
+// triangle) pair of the checked positions is one work item, so a hub with
+// millions of incidences is shared by the whole grid.  ioff[p - plo] is the
+// exclusive prefix of the checked positions' incidence counts; records take
+// their slots from one counter (they are sorted by key and summed afterwards,
+// so their order does not matter).
 
-// edge check, one thread per position of a checked segment
-__global__ void check_edges_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof, const int64_t* sa,
-                                   const int64_t* sb, int32_t npos_lo, int32_t npos_hi, const int64_t* rowptr,
-                                   const int32_t* col, const int64_t* slot_edge, const int32_t* eu, const int64_t* W,
-                                   int64_t Dn, int32_t n, int32_t nact, int64_t* deltaS, Rec rec, bool count_only) {
+__global__ void inc_count_kernel(const int32_t* order, const int32_t* segof, int32_t plo, int32_t phi,
+                                 const int64_t* ptr, int32_t nact, int64_t* icnt) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
-        int32_t s = segof[p];
-        if (s < 0) continue;
-        int32_t x = order[p];
-        if (x < nact) {                              // isolated vertices have no row
-            int64_t a = sa[s], b = sb[s];
-            int64_t d = 0, c = 0;
-            int64_t o = count_only ? 0 : rec.off[p - npos_lo];
-            for (int64_t q = rowptr[x], e = rowptr[x + 1]; q < e; ++q) {
-                int32_t y = col[q];
-                int64_t py = pos[y];
-                if (py >= a && py <= b) continue;
-                if (count_only) {
-                    ++c;
-                    continue;
-                }
-                int64_t ed = slot_edge[q];
-                int64_t share_x = (eu[ed] == x) ? W[ed] : Dn - W[ed];
-                int64_t share_y = Dn - share_x;
-                rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)y;
-                if (py < a) {                        // y in X: the edge goes to x
-                    d += share_y;
-                    rec.val[o] = -share_y;
-                } else {                             // y in Z: the edge goes to y
-                    d -= share_x;
-                    rec.val[o] = share_x;
-                }
-                ++o;
-            }
-            if (count_only) rec.cnt[p - npos_lo] = c;
-            else deltaS[p - npos_lo] = d;
+    for (int64_t p = plo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < phi; p += stride) {
+        const int32_t x = order[p];
+        icnt[p - plo] = ((!segof || segof[p] >= 0) && x < nact) ? ptr[x + 1] - ptr[x] : 0;
+    }
+}
+
+// position of incidence i: the last p with ioff[p - plo] <= i
+__device__ __forceinline__ int64_t inc_position(const int64_t* ioff, int32_t plo, int32_t phi, int64_t i) {
+    int64_t lo = 0, hi = phi - plo;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ioff[mid] <= i) lo = mid; else hi = mid;
+    }
+    return plo + lo;
+}
+
+__global__ void check_edges_flat_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof,
+                                        const int64_t* sa, const int64_t* sb, int32_t plo, int32_t phi,
+                                        const int64_t* ioff, int64_t ninc, const int64_t* rowptr, const int32_t* col,
+                                        const int64_t* slot_edge, const int32_t* eu, const int64_t* W, int64_t Dn,
+                                        int32_t n, unsigned long long* deltaS, uint64_t* rkey, int64_t* rval,
+                                        unsigned long long* nrec) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ninc; i += stride) {
+        const int64_t p = inc_position(ioff, plo, phi, i);
+        const int32_t s = segof[p];
+        const int32_t x = order[p];
+        const int64_t q = rowptr[x] + (i - ioff[p - plo]);
+        const int32_t y = col[q];
+        const int64_t py = pos[y], a = sa[s], b = sb[s];
+        if (py >= a && py <= b) continue;
+        const int64_t ed = slot_edge[q];
+        const int64_t share_x = (eu[ed] == x) ? W[ed] : Dn - W[ed];
+        const int64_t share_y = Dn - share_x;
+        const unsigned long long o = atomicAdd(nrec, 1ull);
+        rkey[o] = (uint64_t)s * (uint64_t)n + (uint64_t)y;
+        if (py < a) {                                // y in X: the edge goes to x
+            atomicAdd(deltaS + (p - plo), (unsigned long long)share_y);
+            rval[o] = -share_y;
+        } else {                                     // y in Z: the edge goes to y
+            atomicAdd(deltaS + (p - plo), (unsigned long long)(-share_x));
+            rval[o] = share_x;
         }
     }
 }
 
-// triangle check: a triangle touching segment s is handled by its member of s
-// with the largest position
-__global__ void check_tris_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof, const int64_t* sa,
-                                  const int64_t* sb, int32_t npos_lo, int32_t npos_hi, const int64_t* vt_ptr,
-                                  const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
-                                  const int64_t* W, int32_t n, int32_t nact, unsigned long long* deltaS, Rec rec,
-                                  bool count_only) {
+// a triangle touching segment s is handled by its member of s with the largest position
+__global__ void check_tris_flat_kernel(const int32_t* order, const int32_t* pos, const int32_t* segof,
+                                       const int64_t* sa, const int64_t* sb, int32_t plo, int32_t phi,
+                                       const int64_t* ioff, int64_t ninc, const int64_t* vt_ptr,
+                                       const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                       const int64_t* W, int32_t n, unsigned long long* deltaS, uint64_t* rkey,
+                                       int64_t* rval, unsigned long long* nrec) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = npos_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npos_hi; p += stride) {
-        int32_t s = segof[p];
-        if (s < 0) continue;
-        int32_t x = order[p];
-        if (x >= nact) continue;                     // isolated vertices lie in no triangle
-        int64_t a = sa[s], b = sb[s];
-        int64_t c = 0;
-        int64_t o = count_only ? 0 : rec.off[p - npos_lo];
-        for (int64_t q = vt_ptr[x], e = vt_ptr[x + 1]; q < e; ++q) {
-            int32_t t = vt_idx[q];
-            int32_t v[3] = {ta[t], tb[t], tc[t]};
-            int64_t pp[3] = {pos[v[0]], pos[v[1]], pos[v[2]]};
-            // owner: the member of s with the largest position
-            int64_t best = -1;
-            for (int k = 0; k < 3; ++k)
-                if (pp[k] >= a && pp[k] <= b && pp[k] > best) best = pp[k];
-            if (best != p) continue;
-            int zt = -1, st = -1;
-            bool anyx = false;
-            for (int k = 0; k < 3; ++k) {
-                if (pp[k] > b) { if (zt < 0 || pp[k] > pp[zt]) zt = k; }
-                else if (pp[k] < a) anyx = true;
-                else if (st < 0 || pp[k] > pp[st]) st = k;
-            }
-            int tgt;
-            if (zt >= 0) tgt = zt;
-            else if (anyx) tgt = st;
-            else continue;
-            int64_t moved = 0;
-            for (int k = 0; k < 3; ++k) {
-                bool mover = (zt >= 0) ? !(pp[k] > b) : (pp[k] < a);
-                if (!mover) continue;
-                int64_t w = W[3 * (int64_t)t + k];
-                moved += w;
-                if (pp[k] >= a && pp[k] <= b) {
-                    if (!count_only) atomicAdd(deltaS + (pp[k] - npos_lo), (unsigned long long)(-w));
-                } else if (count_only) {
-                    ++c;
-                } else {
-                    rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[k];
-                    rec.val[o++] = -w;
-                }
-            }
-            if (pp[tgt] >= a && pp[tgt] <= b) {
-                if (!count_only) atomicAdd(deltaS + (pp[tgt] - npos_lo), (unsigned long long)moved);
-            } else if (count_only) {
-                ++c;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ninc; i += stride) {
+        const int64_t p = inc_position(ioff, plo, phi, i);
+        const int32_t s = segof[p];
+        const int32_t x = order[p];
+        const int32_t t = vt_idx[vt_ptr[x] + (i - ioff[p - plo])];
+        const int64_t a = sa[s], b = sb[s];
+        const int32_t v[3] = {ta[t], tb[t], tc[t]};
+        const int64_t pp[3] = {pos[v[0]], pos[v[1]], pos[v[2]]};
+        int64_t best = -1;
+        for (int k = 0; k < 3; ++k)
+            if (pp[k] >= a && pp[k] <= b && pp[k] > best) best = pp[k];
+        if (best != p) continue;
+        int zt = -1, st = -1;
+        bool anyx = false;
+        for (int k = 0; k < 3; ++k) {
+            if (pp[k] > b) { if (zt < 0 || pp[k] > pp[zt]) zt = k; }
+            else if (pp[k] < a) anyx = true;
+            else if (st < 0 || pp[k] > pp[st]) st = k;
+        }
+        int tgt;
+        if (zt >= 0) tgt = zt;
+        else if (anyx) tgt = st;
+        else continue;
+        int64_t moved = 0;
+        for (int k = 0; k < 3; ++k) {
+            const bool mover = (zt >= 0) ? !(pp[k] > b) : (pp[k] < a);
+            if (!mover) continue;
+            const int64_t w = W[3 * (int64_t)t + k];
+            moved += w;
+            if (pp[k] >= a && pp[k] <= b) {
+                atomicAdd(deltaS + (pp[k] - plo), (unsigned long long)(-w));
             } else {
-                rec.key[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[tgt];
-                rec.val[o++] = moved;
+                const unsigned long long o = atomicAdd(nrec, 1ull);
+                rkey[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[k];
+                rval[o] = -w;
             }
         }
-        if (count_only) rec.cnt[p - npos_lo] = c;
+        if (pp[tgt] >= a && pp[tgt] <= b) {
+            atomicAdd(deltaS + (pp[tgt] - plo), (unsigned long long)moved);
+        } else {
+            const unsigned long long o = atomicAdd(nrec, 1ull);
+            rkey[o] = (uint64_t)s * (uint64_t)n + (uint64_t)v[tgt];
+            rval[o] = moved;
+        }
+    }
+}
+
+// ---- incremental chain checks.  For a fixed start a the candidate segment S =
+// [a, b] grows; a pattern's change of the loads (its "delta") depends only on
+// which of its members lie before S (X), in S or after S (Z):
+//   * no member in S: unchanged;
+//   * a member in Z: every member outside Z gives its weight to the Z member of
+//     largest position (the lowest load in Z);
+//   * else a member in X: every X member gives its weight to the S member of
+//     largest position;
+//   * else (all in S): unchanged.
+// Growing S from [a, b] to [a, b'] changes the category of the members in
+// (b, b'] only, so the per-position deltas are updated by (new - old) for the
+// patterns with a member there, each pattern once (by its member of largest
+// position in (b, b']).
+
+__device__ __forceinline__ void pattern_delta(int k, const int64_t* pp, const int64_t* w, int64_t a, int64_t b,
+                                              int64_t* d) {
+    int zt = -1, st = -1;
+    bool anyx = false, anys = false;
+    for (int j = 0; j < k; ++j) {
+        d[j] = 0;
+        if (pp[j] > b) { if (zt < 0 || pp[j] > pp[zt]) zt = j; }
+        else if (pp[j] < a) anyx = true;
+        else { anys = true; if (st < 0 || pp[j] > pp[st]) st = j; }
+    }
+    if (!anys || (zt < 0 && !anyx)) return;
+    const int tgt = zt >= 0 ? zt : st;
+    int64_t moved = 0;
+    for (int j = 0; j < k; ++j) {
+        const bool mover = zt >= 0 ? !(pp[j] > b) : (pp[j] < a);
+        if (mover) {
+            d[j] -= w[j];
+            moved += w[j];
+        }
+    }
+    d[tgt] += moved;
+}
+
+__global__ void chain_extend_kernel(bool tri, const int32_t* order, const int32_t* pos, int64_t a, int64_t b0,
+                                    int64_t b1, const int64_t* ioff, int64_t ninc, const int64_t* rowptr,
+                                    const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
+                                    const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta,
+                                    const int32_t* tb, const int32_t* tc, const int64_t* W, int64_t Dn,
+                                    unsigned long long* delta) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int32_t plo = (int32_t)(b0 + 1), phi = (int32_t)(b1 + 1);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ninc; i += stride) {
+        const int64_t p = inc_position(ioff, plo, phi, i);
+        const int32_t x = order[p];
+        const int64_t r = i - ioff[p - plo];
+        int k;
+        int64_t pp[3], w[3];
+        if (tri) {
+            const int32_t t = vt_idx[vt_ptr[x] + r];
+            const int32_t v[3] = {ta[t], tb[t], tc[t]};
+            k = 3;
+            for (int j = 0; j < 3; ++j) {
+                pp[j] = pos[v[j]];
+                w[j] = W[3 * (int64_t)t + j];
+            }
+        } else {
+            const int64_t q = rowptr[x] + r;
+            const int32_t y = col[q];
+            const int64_t ed = slot_edge[q];
+            k = 2;
+            pp[0] = p;
+            pp[1] = pos[y];
+            w[0] = (eu[ed] == x) ? W[ed] : Dn - W[ed];
+            w[1] = Dn - w[0];
+        }
+        // the pattern is handled by its member of largest position in (b0, b1]
+        int64_t best = -1;
+        for (int j = 0; j < k; ++j)
+            if (pp[j] > b0 && pp[j] <= b1 && pp[j] > best) best = pp[j];
+        if (best != p) continue;
+        int64_t dn[3], dold[3];
+        pattern_delta(k, pp, w, a, b1, dn);
+        pattern_delta(k, pp, w, a, b0, dold);
+        for (int j = 0; j < k; ++j)
+            if (dn[j] != dold[j]) atomicAdd(delta + pp[j], (unsigned long long)(dn[j] - dold[j]));
+    }
+}
+
+// min / max of R + delta over X = [0, a), S = [a, b], Z = (b, n); out = {minS, maxS, minX, maxZ},
+// loads are nonnegative so unsigned atomics order them
+__global__ void chain_extremes_kernel(const int32_t* order, const int64_t* R, const int64_t* delta, int32_t n,
+                                      int64_t a, int64_t b, unsigned long long* out) {
+    __shared__ unsigned long long sh[4][32];
+    unsigned long long mnS = ~0ull, mxS = 0, mnX = ~0ull, mxZ = 0;
+    bool hasZ = false;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const unsigned long long v = (unsigned long long)(R[order[p]] + delta[p]);
+        if (p < a) mnX = min(mnX, v);
+        else if (p <= b) { mnS = min(mnS, v); mxS = max(mxS, v); }
+        else { mxZ = max(mxZ, v); hasZ = true; }
+    }
+    (void)hasZ;
+    for (int o = 16; o; o >>= 1) {
+        mnS = min(mnS, __shfl_xor_sync(0xffffffffu, mnS, o));
+        mxS = max(mxS, __shfl_xor_sync(0xffffffffu, mxS, o));
+        mnX = min(mnX, __shfl_xor_sync(0xffffffffu, mnX, o));
+        mxZ = max(mxZ, __shfl_xor_sync(0xffffffffu, mxZ, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sh[0][wid] = mnS; sh[1][wid] = mxS; sh[2][wid] = mnX; sh[3][wid] = mxZ; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int j = 1; j < nw; ++j) {
+            mnS = min(mnS, sh[0][j]); mxS = max(mxS, sh[1][j]);
+            mnX = min(mnX, sh[2][j]); mxZ = max(mxZ, sh[3][j]);
+        }
+        atomicMin(out + 0, mnS);
+        atomicMax(out + 1, mxS);
+        atomicMin(out + 2, mnX);
+        atomicMax(out + 3, mxZ);
     }
 }
 
@@ -428,32 +544,41 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
     LDS_CUDA(cudaMemsetAsync(deltaS.get(), 0, (phi - plo) * sizeof(int64_t), s));
     const int64_t* W = g->fw_W.get();
     const int32_t nact = g->nact;
-    // two passes: count the records of every position, then fill an exactly sized buffer
+    // every incidence of a checked position is one work item; each emits at most one
+    // record (edges) or owns at most one triangle, which emits at most two
     DevBuf<uint64_t> rkey;
     DevBuf<int64_t> rval;
-    DevBuf<int64_t> rcnt(phi - plo, s), roff(phi - plo, s);
-    LDS_CUDA(cudaMemsetAsync(rcnt.get(), 0, (phi - plo) * sizeof(int64_t), s));
     int64_t nrec = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool count_only = pass == 0;
-        if (!count_only) {
-            nrec = exclusive_scan_i64(rcnt.get(), roff.get(), phi - plo, s);
-            rkey.alloc(std::max<int64_t>(nrec, 1), s);
-            rval.alloc(std::max<int64_t>(nrec, 1), s);
-        }
-        Rec rec{rkey.get(), rval.get(), rcnt.get(), roff.get()};
-        if (!tri) {
-            if (g->m) {
-                ensure_slot_edge(g);
-                LDS_LAUNCH(check_edges_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(),
-                           segof, sa.get(), sb.get(), plo, phi, g->rowptr.get(), g->col.get(), g->slot_edge.get(),
-                           g->eu.get(), W, g->fw_D, n, nact, deltaS.get(), rec, count_only);
-            }
-        } else if (g->ntri) {
-            ensure_vertex_triangles(g);
-            LDS_LAUNCH(check_tris_kernel, grid_for(phi - plo, 128), 128, 0, s, st.order.get(), st.pos.get(), segof,
-                       sa.get(), sb.get(), plo, phi, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(), g->tb.get(),
-                       g->tc.get(), W, n, nact, (unsigned long long*)deltaS.get(), rec, count_only);
+    const bool have = tri ? g->ntri > 0 : g->m > 0;
+    if (have) {
+        if (tri) ensure_vertex_triangles(g);
+        else ensure_slot_edge(g);
+        const int64_t* iptr = tri ? g->vt_ptr.get() : g->rowptr.get();
+        DevBuf<int64_t> icnt(phi - plo, s), ioff(phi - plo, s);
+        LDS_LAUNCH(inc_count_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), segof, plo, phi, iptr, nact,
+                   icnt.get());
+        const int64_t ninc = exclusive_scan_i64(icnt.get(), ioff.get(), phi - plo, s);
+        if (ninc) {
+            const int64_t cap = tri ? 2 * ninc : ninc;
+            rkey.alloc(cap, s);
+            rval.alloc(cap, s);
+            DevBuf<unsigned long long> dn(1, s);
+            LDS_CUDA(cudaMemsetAsync(dn.get(), 0, sizeof(unsigned long long), s));
+            if (tri)
+                LDS_LAUNCH(check_tris_flat_kernel, grid_for(ninc, blk), blk, 0, s, st.order.get(), st.pos.get(), segof,
+                           sa.get(), sb.get(), plo, phi, ioff.get(), ninc, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(),
+                           g->tb.get(), g->tc.get(), W, n, (unsigned long long*)deltaS.get(), rkey.get(), rval.get(),
+                           dn.get());
+            else
+                LDS_LAUNCH(check_edges_flat_kernel, grid_for(ninc, blk), blk, 0, s, st.order.get(), st.pos.get(), segof,
+                           sa.get(), sb.get(), plo, phi, ioff.get(), ninc, g->rowptr.get(), g->col.get(),
+                           g->slot_edge.get(), g->eu.get(), W, g->fw_D, n, (unsigned long long*)deltaS.get(),
+                           rkey.get(), rval.get(), dn.get());
+            unsigned long long hn = 0;
+            LDS_CUDA(cudaMemcpyAsync(&hn, dn.get(), sizeof(hn), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            nrec = (int64_t)hn;
+            LDS_REQUIRE(nrec <= cap, LDS_ECUDA, "extract_sg: record buffer overrun");
         }
     }
     DevBuf<long long> dminS(nseg, s), dmaxS(nseg, s), dminX(nseg, s), dmaxZ(nseg, s);
@@ -483,6 +608,65 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
     LDS_CUDA(cudaMemcpyAsync(maxZ.data(), dmaxZ.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
 }
+
+// A growing segment [a, b] of one chain of merged candidates (see chain_extend_kernel).
+struct Chain {
+    lds_graph* g;
+    const SgState& st;
+    DevBuf<int64_t> delta;
+    DevBuf<unsigned long long> ext;
+    int64_t a = -1, b = -1;
+    Chain(lds_graph* gg, const SgState& s_) : g(gg), st(s_) {}
+
+    void begin(int64_t start) {
+        cudaStream_t s = g->stream;
+        const int32_t n = g->n;
+        if (!delta.p) {
+            delta.alloc(n, s);
+            ext.alloc(4, s);
+        }
+        LDS_CUDA(cudaMemsetAsync(delta.get(), 0, n * sizeof(int64_t), s));
+        a = start;
+        b = start - 1;
+    }
+
+    // grows S to [a, b1]; returns (minS, maxS, minX, maxZ) of the modified loads
+    void extend(int64_t b1, long long out[4]) {
+        cudaStream_t s = g->stream;
+        const int blk = 256;
+        const int32_t n = g->n, nact = g->nact;
+        const bool tri = g->fw_density == LDS_TRIANGLE;
+        const int32_t plo = (int32_t)(b + 1), phi = (int32_t)(b1 + 1);
+        if ((tri && g->ntri) || (!tri && g->m)) {
+            if (tri) ensure_vertex_triangles(g);
+            else ensure_slot_edge(g);
+            const int64_t* iptr = tri ? g->vt_ptr.get() : g->rowptr.get();
+            // every position in (b, b1] is walked (no segment map)
+            DevBuf<int64_t> icnt(phi - plo, s), ioff(phi - plo, s);
+            LDS_LAUNCH(inc_count_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), (const int32_t*)nullptr,
+                       plo, phi, iptr, nact, icnt.get());
+            const int64_t ninc = exclusive_scan_i64(icnt.get(), ioff.get(), phi - plo, s);
+            if (ninc)
+                LDS_LAUNCH(chain_extend_kernel, grid_for(ninc, blk), blk, 0, s, tri, st.order.get(), st.pos.get(), a, b,
+                           b1, ioff.get(), ninc, g->rowptr.get(), g->col.get(), tri ? nullptr : g->slot_edge.get(),
+                           g->eu.get(), tri ? g->vt_ptr.get() : nullptr, tri ? g->vt_idx.get() : nullptr,
+                           g->ta.get(), g->tb.get(), g->tc.get(), g->fw_W.get(), g->fw_D,
+                           (unsigned long long*)delta.get());
+        }
+        b = b1;
+        const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
+        LDS_CUDA(cudaMemcpyAsync(ext.get(), init, sizeof(init), cudaMemcpyHostToDevice, s));
+        LDS_LAUNCH(chain_extremes_kernel, grid_for(n, blk), blk, 0, s, st.order.get(), g->fw_R.get(), delta.get(), n,
+                   a, b, ext.get());
+        unsigned long long h[4];
+        LDS_CUDA(cudaMemcpyAsync(h, ext.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        out[0] = (long long)h[0];
+        out[1] = (long long)h[1];
+        out[2] = h[2] == ~0ull ? LLONG_MAX : (long long)h[2];
+        out[3] = b == n - 1 ? LLONG_MIN : (long long)h[3];
+    }
+};
 
 void extract_sg(lds_graph* g, SgState& st) {
     LDS_REQUIRE(g->fw_valid, LDS_EINVAL, "extract_sg: run lds_fw on this graph first");
@@ -580,6 +764,9 @@ void extract_sg(lds_graph* g, SgState& st) {
     // For a fixed start, growing the segment only lowers the X vertices' modified
     // loads and only raises max_S r': once the X-side test fails it fails for
     // every longer merge, so the whole rest is the unaccepted remainder.
+    // Merged candidates of one start are checked incrementally (Chain): each step
+    // only walks the patterns of the positions it adds.
+    Chain chain(g, st);
     int64_t start = 0;
     for (size_t k = 0; k < ca.size(); ++k) {
         long long lo, hi, mx, mz;
@@ -587,10 +774,10 @@ void extract_sg(lds_graph* g, SgState& st) {
             ensure_checked(k);
             lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
-            std::vector<int64_t> a1{start}, b1{cb[k]};
-            std::vector<long long> s1, s2, s3, s4;
-            check_segments(g, st, segof.get(), a1, b1, s1, s2, s3, s4);
-            lo = s1[0]; hi = s2[0]; mx = s3[0]; mz = s4[0];
+            if (chain.a != start) chain.begin(start);
+            long long e[4];
+            chain.extend(cb[k], e);
+            lo = e[0]; hi = e[1]; mx = e[2]; mz = e[3];
             ++st.chain_checks;
         }
         const bool xok = start == 0 || mx > hi;
