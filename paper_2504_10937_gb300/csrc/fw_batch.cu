@@ -16,6 +16,8 @@
 // path.
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <unordered_set>
 #include <vector>
 
@@ -25,8 +27,26 @@ namespace lds {
 
 namespace {
 
-constexpr int FB_THREADS = 1024;
+constexpr int FB_THREADS = 1024;                // threads per graph unless tuned
 constexpr int32_t ONCHIP_MAX_V = 24576;          // 8 B of shared memory per vertex
+constexpr int kThreadChoices[] = {128, 256, 512, 1024};
+
+// threads per graph (warps per graph x 32) chosen per size bucket: the bit
+// length of the graph's active vertex count
+std::mutex g_fwb_mu;
+std::map<int, int> g_fwb_threads;
+
+int fwb_bucket(int32_t nact) {
+    int b = 0;
+    while (nact) { ++b; nact >>= 1; }
+    return b;
+}
+
+int fwb_threads_for(int bucket) {
+    std::lock_guard<std::mutex> lk(g_fwb_mu);
+    auto it = g_fwb_threads.find(bucket);
+    return it == g_fwb_threads.end() ? FB_THREADS : it->second;
+}
 
 struct GraphJob {
     const int32_t* eu;
@@ -41,7 +61,7 @@ struct GraphJob {
 };
 
 template <bool FP32>
-__global__ void __launch_bounds__(FB_THREADS, 1)
+__global__ void __launch_bounds__(FB_THREADS)
     fw_batch_kernel(const GraphJob* __restrict__ jobs, int32_t njobs, int32_t* next, int32_t N) {
     extern __shared__ __align__(16) uint32_t sm[];
     __shared__ int32_t job;
@@ -114,6 +134,22 @@ __global__ void __launch_bounds__(FB_THREADS, 1)
     }
 }
 
+void launch_bucket(const GraphJob* jobs, int32_t njobs, int32_t* next, int32_t maxv, int threads, bool fp32,
+                   int32_t iters, cudaStream_t s) {
+    const size_t smem = (size_t)maxv * 8;
+    int per_sm = 0;
+    if (fp32) {
+        LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batch_kernel<true>, threads, smem));
+    } else {
+        LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fw_batch_kernel<false>, threads, smem));
+    }
+    const int grid = std::max(1, std::min(num_sms() * std::max(per_sm, 1), (int)njobs));
+    if (fp32) LDS_LAUNCH(fw_batch_kernel<true>, grid, threads, smem, s, jobs, njobs, next, iters);
+    else LDS_LAUNCH(fw_batch_kernel<false>, grid, threads, smem, s, jobs, njobs, next, iters);
+}
+
 bool fits_on_chip(const lds_graph* g, int32_t N, lds_precision p) {
     if (p != LDS_EXACT && p != LDS_FP32) return false;
     if (N < 1 || g->m < 1 || g->nact > ONCHIP_MAX_V) return false;
@@ -128,9 +164,12 @@ bool fits_on_chip(const lds_graph* g, int32_t N, lds_precision p) {
 
 using namespace lds;
 
-extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p,
-                                   int32_t* onchip) {
-    return guard([&] {
+namespace lds {
+
+// lds_fw_batch's body; force_threads > 0 overrides the tuned threads per graph
+void fw_batch_run(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p, int32_t* onchip,
+                  int force_threads) {
+    {
         LDS_REQUIRE(count >= 0 && (count == 0 || graphs), LDS_EINVAL, "lds_fw_batch: bad graph list");
         LDS_REQUIRE(iters >= 0 && iters <= 60000, LDS_EINVAL, "lds_fw_batch: iters = %d out of range", iters);
         LDS_REQUIRE(p == LDS_EXACT || p == LDS_FP32 || p == LDS_FP64, LDS_EINVAL, "lds_fw_batch: bad precision");
@@ -148,7 +187,11 @@ extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t it
             g->fw_reuse = true;
         }
         if (on.empty()) return;
-        std::sort(on.begin(), on.end(), [](const lds_graph* a, const lds_graph* b) { return a->m > b->m; });
+        // size buckets contiguous (largest first), largest graphs first inside a bucket
+        std::sort(on.begin(), on.end(), [](const lds_graph* a, const lds_graph* b) {
+            const int ba = fwb_bucket(a->nact), bb = fwb_bucket(b->nact);
+            return ba != bb ? ba > bb : a->m > b->m;
+        });
         // each handle's buffers are allocated on its own stream, then everything runs on the first one
         int64_t total_m = 0;
         for (lds_graph* g : on) total_m += g->m;
@@ -171,21 +214,26 @@ extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t it
             off_m += g->m;
             maxv = std::max(maxv, g->nact);
         }
+        (void)maxv;
         DevBuf<GraphJob> djobs(jobs.size(), s);
-        DevBuf<int32_t> next(1, s);
+        DevBuf<int32_t> next(64, s);
         LDS_CUDA(cudaMemcpyAsync(djobs.get(), jobs.data(), jobs.size() * sizeof(GraphJob), cudaMemcpyHostToDevice, s));
-        LDS_CUDA(cudaMemsetAsync(next.get(), 0, sizeof(int32_t), s));
-        const size_t smem = (size_t)maxv * 8;
-        const int grid = std::max(1, std::min(num_sms(), (int)jobs.size()));
+        LDS_CUDA(cudaMemsetAsync(next.get(), 0, 64 * sizeof(int32_t), s));
         const auto t0 = std::chrono::steady_clock::now();
-        if (p == LDS_FP32) {
-            LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            LDS_LAUNCH(fw_batch_kernel<true>, grid, FB_THREADS, smem, s, djobs.get(), (int32_t)jobs.size(), next.get(),
-                       iters);
-        } else {
-            LDS_CUDA(cudaFuncSetAttribute(fw_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            LDS_LAUNCH(fw_batch_kernel<false>, grid, FB_THREADS, smem, s, djobs.get(), (int32_t)jobs.size(), next.get(),
-                       iters);
+        // one launch per size bucket (jobs are sorted by size, so buckets are contiguous):
+        // its own threads per graph and shared memory sized to its largest graph, as
+        // many CTAs per SM as fit
+        size_t lo = 0;
+        int launch = 0;
+        while (lo < on.size()) {
+            const int bk = fwb_bucket(on[lo]->nact);
+            size_t hi = lo;
+            int32_t bmax = 1;
+            while (hi < on.size() && fwb_bucket(on[hi]->nact) == bk) bmax = std::max(bmax, on[hi++]->nact);
+            const int threads = force_threads > 0 ? force_threads : fwb_threads_for(bk);
+            launch_bucket(djobs.get() + lo, (int32_t)(hi - lo), next.get() + (launch++ % 64), bmax, threads,
+                          p == LDS_FP32, iters, s);
+            lo = hi;
         }
         LDS_CUDA(cudaStreamSynchronize(s));
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -204,5 +252,49 @@ extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t it
             g->pass_kernel = "fw_batch_kernel";
         }
         if (onchip) *onchip = (int32_t)on.size();
-    });
+    }
+}
+
+// Times the on-chip Frank-Wolfe of `count` graphs with every threads-per-graph
+// choice, per size bucket, and keeps the fastest choice of each bucket.
+void fw_batch_autotune(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p) {
+    std::map<int, std::vector<lds_graph*>> byb;
+    for (int32_t i = 0; i < count; ++i)
+        if (fits_on_chip(graphs[i], iters, p)) byb[fwb_bucket(graphs[i]->nact)].push_back(graphs[i]);
+    for (auto& kv : byb) {
+        {
+            std::lock_guard<std::mutex> lk(g_fwb_mu);
+            if (g_fwb_threads.count(kv.first)) continue;
+        }
+        double best = 1e300;
+        int best_t = FB_THREADS;
+        for (int t : kThreadChoices) {
+            const auto t0 = std::chrono::steady_clock::now();
+            fw_batch_run((int32_t)kv.second.size(), kv.second.data(), iters, p, nullptr, t);
+            const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (ms < best) {
+                best = ms;
+                best_t = t;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_fwb_mu);
+        g_fwb_threads[kv.first] = best_t;
+    }
+}
+
+int32_t fw_batch_threads(int32_t nact) { return fwb_threads_for(fwb_bucket(nact)); }
+
+}  // namespace lds
+
+extern "C" lds_status lds_fw_batch(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p,
+                                   int32_t* onchip) {
+    return guard([&] { fw_batch_run(count, graphs, iters, p, onchip, 0); });
+}
+
+extern "C" int32_t lds_fw_batch_threads(int32_t nact) {
+    try {
+        return fw_batch_threads(nact);
+    } catch (...) {
+        return 0;
+    }
 }

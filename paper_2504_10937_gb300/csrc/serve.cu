@@ -16,6 +16,7 @@
 // layer: it only schedules queries the paper defines.
 #include <chrono>
 #include <condition_variable>
+#include <map>
 #include <deque>
 #include <memory>
 #include <mutex>
@@ -353,6 +354,18 @@ lds_status lds_batch_autotune(int32_t count, const lds_query* queries, int32_t* 
                 *workers = it->second;
                 return;
             }
+        }
+        // the on-chip first-round Frank-Wolfe: threads per graph for every size bucket of
+        // the batch's edge queries, per iteration count and arithmetic
+        {
+            std::map<std::pair<int32_t, int>, std::vector<lds_graph*>> groups;
+            std::unordered_set<lds_graph*> seen;
+            for (int32_t i = 0; i < count; ++i)
+                if (queries[i].d == LDS_EDGE && seen.insert(queries[i].g).second)
+                    groups[{queries[i].iters, (int)queries[i].p}].push_back(queries[i].g);
+            for (auto& kv : groups)
+                fw_batch_autotune((int32_t)kv.second.size(), kv.second.data(), kv.first.first,
+                                  (lds_precision)kv.first.second);
         }
         // time a sample of the batch with each worker count; keep the fastest
         const int32_t sample = std::min<int32_t>(count, 64);

@@ -124,3 +124,46 @@ def test_server_budget(lds):
             _same(want, got)
     for g, _ in gs:
         g.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_mix():
+    # 64 graphs of the batched mix (20 of them triangle-density queries), small
+    # enough for the CPU oracle's driver (about a minute for all of them)
+    from oracle import ldscvx
+    mix = synth.batched_mix(64, seed=41, n_range=(50, 1500))
+    want = [[(d, list(c)) for d, c in ldscvx.topk(g["n"], g["u"], g["v"], 3, 200 if g["triangle"] else 100,
+                                                  triangle=g["triangle"], precision="fp32")] for g in mix]
+    return mix, want
+
+
+def _lists(res):
+    return [(d, [int(x) for x in c]) for d, c in res]
+
+
+def test_batch_matches_oracle(lds, oracle_mix):
+    # Problem 1 / Problem 2 answers of the batched path against the oracle's
+    # driver, both densities, with the autotuned launch shape
+    mix, want = oracle_mix
+    gs = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
+    queries = [(g, 3, "triangle" if x["triangle"] else "edge", 200 if x["triangle"] else 100, "fp32")
+               for g, x in zip(gs, mix)]
+    workers = lds.batch_autotune(queries)
+    got = lds.topk_batch(queries, workers=workers)
+    assert [_lists(r) for r in got] == want
+    for g in gs:
+        g.close()
+
+
+def test_server_matches_oracle(lds, oracle_mix):
+    # the same queries through the serving loop, all submitted at once so that
+    # they overlap on the device
+    mix, want = oracle_mix
+    gs = [lds.Graph(g["n"], g["u"].astype(np.int32), g["v"].astype(np.int32)) for g in mix]
+    with lds.Server(1 << 34, 8) as srv:
+        tickets = [srv.submit(g, 3, "triangle" if x["triangle"] else "edge", 200 if x["triangle"] else 100, "fp32")
+                   for g, x in zip(gs, mix)]
+        got = [_lists(srv.wait(t)[0]) for t in tickets]
+    assert got == want
+    for g in gs:
+        g.close()
