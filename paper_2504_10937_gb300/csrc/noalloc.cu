@@ -14,7 +14,10 @@
 //   * at most LDS_NOALLOC_MAX_VERTICES vertices; larger n is rejected;
 //   * on each device, the first call resolves the array's device address with
 //     cudaGetSymbolAddress while that device is current; that first call
-//     should come before any stream capture;
+//     should come before any stream capture.  The address is kept per device
+//     ordinal for the life of the process, which assumes the device's primary
+//     context lives as long: after cudaDeviceReset, or with another context
+//     current on the same ordinal, the kept address is stale;
 //   * every call on a device shares the array and leaves its last contents in
 //     it; each call clears the part it uses first, so calls that overlap on the
 //     GPU (different streams, concurrent host threads) race and must not be
@@ -59,13 +62,15 @@ __global__ void noalloc_clear_kernel(int32_t* scratch, int64_t* R, int32_t n) {
 }
 
 // R_x = deg(x) (alpha = 1/2 scaled by D_0 = 2), W_e = 1; flags ids that are out
-// of range or not ordered u < v.
+// of range or not ordered u < v, and edges that are not strictly after the
+// previous one in (u, v) order (a repeat or an unsorted list).
 __global__ void noalloc_init_kernel(const int32_t* u, const int32_t* v, int64_t m, int32_t n, int64_t* R, int64_t* W,
                                     int32_t* scratch) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         int32_t a = u[e], b = v[e];
-        if (a < 0 || b >= n || a >= b) {
+        const bool ordered = e == 0 || u[e - 1] < a || (u[e - 1] == a && v[e - 1] < b);
+        if (a < 0 || b >= n || a >= b || !ordered) {
             atomicOr(scratch + kErrorWord, 1);
             continue;
         }
@@ -120,7 +125,8 @@ extern "C" lds_status lds_fw_exact_noalloc(int32_t n, int64_t m, const int32_t* 
         int32_t bad = 0;
         LDS_CUDA(cudaMemcpyAsync(&bad, scratch + kErrorWord, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
-        LDS_REQUIRE(!bad, LDS_EINVAL, "lds_fw_exact_noalloc: edge ids must satisfy 0 <= u < v < n");
+        LDS_REQUIRE(!bad, LDS_EINVAL,
+                    "lds_fw_exact_noalloc: edges must satisfy 0 <= u < v < n and be distinct and sorted by (u, v)");
         for (int32_t i = 1; i <= iters && m; ++i) {
             const int64_t inc = 2 * (int64_t)(i + 1);
             LDS_LAUNCH(noalloc_pass_kernel, grid_for(m, blk), blk, 0, s, u, v, m, R, W, inc, scratch);

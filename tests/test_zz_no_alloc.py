@@ -41,6 +41,14 @@ def test_noalloc_matches_lds_fw_on_two_calls():
             torch.cuda.synchronize()
             assert np.array_equal(R.cpu().numpy(), ref["R"])
             assert np.array_equal(W.cpu().numpy(), ref["W"])
+    # a repeated edge and an unsorted list are refused (both would silently
+    # differ from lds_fw on the same graph)
+    for perm in (np.r_[0, np.arange(m - 1)], np.r_[1, 0, np.arange(2, m)]):
+        pu = torch.from_numpy(u[perm].astype(np.int32)).cuda()
+        pv = torch.from_numpy(v[perm].astype(np.int32)).cuda()
+        st = fn(n, m, pu.data_ptr(), pv.data_ptr(), 3, R.data_ptr(), W.data_ptr(), stream)
+        assert st == lds.EINVAL
+        assert b"sorted" in lib.lds_last_error()
     # sizes beyond the fixed scratch are refused, and nothing is launched for them
     big = (1 << 20) + 1
     st = fn(big, 0, None, None, 1, R.data_ptr(), None, stream)
