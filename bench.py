@@ -38,11 +38,71 @@ from paper_2504_10937_gb300 import synth  # noqa: E402
 
 METRIC = "FW edge-updates/s"
 UNIT = "edge-updates/s"
+METRIC_TRI = "FW triangle-updates/s"
+UNIT_TRI = "triangle-updates/s"
 
-# DRAM bytes (read + write) of one launch of the pass kernel on this workload, from
-# one ncu capture of the current kernel (profiles/fw_opass32_chung_lu_1m.md); a
-# kernel changed since then has no entry and reports null.
-PASS_TRAFFIC = {("fw_opass32_kernel", "exact"): 20494336}
+# DRAM bytes (read + write) of one launch of the FW pass kernel on this workload,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# the kernel, the arithmetic and a digest of the source file the kernel was built
+# from at capture time.  A kernel whose source changed since has no matching entry
+# and reports null.
+PASS_TRAFFIC = {}
+PASS_SOURCE = {"fw_opass32_kernel": "paper_2504_10937_gb300/csrc/fw_oriented.cu",
+               "fw_coop32_kernel": "paper_2504_10937_gb300/csrc/fw_oriented.cu",
+               "fw_tri_pass_kernel": "paper_2504_10937_gb300/csrc/fw.cu"}
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _source_digest(kernel: str):
+    import hashlib
+    path = PASS_SOURCE.get(kernel)
+    if not path or not os.path.exists(os.path.join(ROOT, path)):
+        return None
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(kernel: str, precision: str):
+    return PASS_TRAFFIC.get((kernel, precision, _source_digest(kernel)))
+
+
+def _host():
+    """Host CPU description: logical cores and the model name lscpu reports."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _golden_sets(name):
+    """Expected sets written by tests/golden/make_topk_golden.py, or None."""
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        return None
+    out = []
+    with open(path) as f:
+        for ln in f:
+            ln = ln.split("#")[0].strip()
+            if ln:
+                d, vs = ln.split(":")
+                out.append((d.strip(), tuple(int(x) for x in vs.split(","))))
+    return out
+
+
+def _fw_sample(name):
+    """Oracle FW values on a vertex sample (tests/golden/make_fw_sample.py): ids, R, r64."""
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        return None
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return (np.array([int(r[0]) for r in rows]), [int(r[1]) for r in rows],
+            np.array([float(r[2]) for r in rows]))
 
 
 def _peaks():
@@ -54,16 +114,31 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+WORKLOADS = {
+    # power-law: top-10 LDS, 500 iterations, exact arithmetic
+    "chung_lu_1m": dict(density="edge", k=10, iters=500, precision="exact", seed=2, scramble=20,
+                        desc="chung_lu_n1e6_m1e7_exp2.1_50blocks (seed 2), raw COO with 5% repeats and 1% self-loops"),
+    # R-MAT scale 20: top-5 LTDS, 300 iterations, binary32 loads; includes triangle listing
+    "rmat20": dict(density="triangle", k=5, iters=300, precision="fp32", seed=3, scramble=30,
+                   desc="rmat_scale20_ef16_(0.57,0.19,0.19)_20cliques_30-200_p0.8 (seed 3), raw COO with 5% "
+                        "repeats and 1% self-loops; triangle listing inside the step"),
+}
+
+
 def _workload(args):
     """The seeded input; cached under the system temp directory between runs
     of this script on the same machine (the cache holds generator output only)."""
     import tempfile
-    path = os.path.join(tempfile.gettempdir(), "lds_bench_chung_lu_1m_seed2.npz")
+    spec = WORKLOADS[args.workload]
+    path = os.path.join(tempfile.gettempdir(), f"lds_bench_{args.workload}_seed{spec['seed']}.npz")
     if os.path.exists(path):
         d = np.load(path)
         return int(d["n"]), d["u"], d["v"], d["a"], d["b"]
-    n, u, v, blocks = synth.workload_chung_lu_1m(seed=2)
-    a, b = synth.scramble(n, u, v, seed=20)
+    if args.workload == "rmat20":
+        n, u, v, blocks = synth.workload_rmat20(seed=spec["seed"])
+    else:
+        n, u, v, blocks = synth.workload_chung_lu_1m(seed=spec["seed"])
+    a, b = synth.scramble(n, u, v, seed=spec["scramble"])
     try:
         np.savez(path, n=n, u=u, v=v, a=a, b=b)
     except OSError:
@@ -159,35 +234,50 @@ def run_reference(args):
     u64 = u.astype(np.int64)
     v64 = v.astype(np.int64)
     m = len(u)
+    tri = args.density == "triangle"
+    if tri:
+        tris, nsamp = _tri_sample(n, u, v)
+        units = len(tris)
+        sample = (f"{args.ref_iters} exact triangle FW iterations per step on the {units} triangles induced by "
+                  f"the vertices with id < {nsamp} (listing untimed)")
+    else:
+        units = m
+        sample = f"{args.ref_iters} exact FW iterations per step on the full graph (m={m})"
     iters_per_step = args.ref_iters
     times = []
     R, W = None, None
     i = 0
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        R, W, _, _ = ofw.fw_edge_exact(n, u64, v64, i + iters_per_step, R0=R, W0=W, i0=i)
+        if tri:
+            R, W, _, _ = ofw.fw_tri_exact(nsamp, tris, i + iters_per_step, R0=R, W0=W, i0=i)
+        else:
+            R, W, _, _ = ofw.fw_edge_exact(n, u64, v64, i + iters_per_step, R0=R, W0=W, i0=i)
         dt = time.perf_counter() - t0
         i += iters_per_step
         if step >= args.warmup:
             times.append(dt)
     total = sum(times)
-    value = m * iters_per_step * len(times) / total
+    value = units * iters_per_step * len(times) / total
+    unit = UNIT_TRI if tri else UNIT
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "impl": "reference", "metric": METRIC_TRI if tri else METRIC, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": _config(args, n, m),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{iters_per_step} exact FW iterations per step on the full graph (m={m})"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "host": _host(),
+                         "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def _config(args, n, m):
-    return {"workload": "chung_lu_n1e6_m1e7_exp2.1_50blocks (seed 2), raw COO with 5% repeats and 1% self-loops",
-            "n": n, "m": m, "iters": args.iters, "precision": args.precision, "density": "edge", "k": args.k,
-            "step": "ingest + Frank-Wolfe" if getattr(args, "fw_only", False) else "top-k LDS query (lds_topk)",
+    tri = args.density == "triangle"
+    return {"workload": WORKLOADS[args.workload]["desc"],
+            "n": n, "m": m, "iters": args.iters, "precision": args.precision, "density": args.density, "k": args.k,
+            "step": ("ingest + Frank-Wolfe" if getattr(args, "fw_only", False)
+                     else f"top-k {'LTDS' if tri else 'LDS'} query (lds_topk)"),
             "l2": "flushed between steps (512 MiB device write)", "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -202,8 +292,36 @@ def cpu_baseline(n, u, v, budget_s=12.0):
     t0 = time.perf_counter()
     ofw.fw_edge_exact(n, u64, v64, 1 + iters, R0=R, W0=W, i0=1)
     dt = time.perf_counter() - t0
-    return {"value": len(u) * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": len(u) * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host(),
             "sample": f"{iters} exact FW iterations (iterations 2..{iters + 1}) of the oracle on the full graph"}
+
+
+def _tri_sample(n, u, v):
+    """Triangles of the subgraph induced by the vertices with id < n / 8 (ids are
+    randomly relabelled, so this is a seeded random vertex sample), listed by the
+    oracle; listing all triangles of the full graph is far beyond a bounded sample."""
+    from oracle.graph import triangles
+    lim = max(1, n // 8)
+    keep = (u < lim) & (v < lim)
+    return triangles(lim, u[keep].astype(np.int64), v[keep].astype(np.int64)), lim
+
+
+def cpu_baseline_tri(n, u, v, budget_s=12.0):
+    """The oracle's exact triangle FW (Alg. 6) on the host, on the triangles of
+    a vertex sample (listing not timed), for a bounded number of iterations."""
+    from oracle import fw as ofw
+    tris, lim = _tri_sample(n, u, v)
+    n = lim
+    t0 = time.perf_counter()
+    R, W, _, _ = ofw.fw_tri_exact(n, tris, 1)
+    one = time.perf_counter() - t0
+    iters = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    ofw.fw_tri_exact(n, tris, 1 + iters, R0=R, W0=W, i0=1)
+    dt = time.perf_counter() - t0
+    return {"value": len(tris) * iters / dt, "unit": UNIT_TRI, "cores": 1, "kind": "oracle", "host": _host(),
+            "sample": f"{iters} exact triangle FW iterations of the oracle on the {len(tris)} triangles induced "
+                      f"by the vertices with id < {lim}"}
 
 
 def run_ours(args):
@@ -230,11 +348,12 @@ def run_ours(args):
         g = lds.Graph(n, ta, tb, stream=sptr)
         m_holder["m"] = g.m
         if args.fw_only:
-            g.fw(args.iters, precision=args.precision, want=())
-            st = {"fw_edge_updates": g.m * args.iters}
+            g.fw(args.iters, density=args.density, precision=args.precision, want=())
+            st = {"fw_edge_updates": (g.m if args.density == "edge" else g.list_triangles()) * args.iters}
         else:
-            m_holder["result"] = g.topk(args.k, "edge", args.iters, args.precision)
+            m_holder["result"] = g.topk(args.k, args.density, args.iters, args.precision)
             st = lds.topk_last_stats()
+        m_holder["units"] = g.m if args.density == "edge" else g.list_triangles()
         t = g.fw_timing()
         g.close()
         t["stats"] = st
@@ -244,8 +363,9 @@ def run_ours(args):
         step()
         flush.zero_()
     torch.cuda.synchronize()
-    lds.set_pass_profiling(True)
-    times, pass_us, fw_ms, updates, phase = [], [], [], [], []
+    # the timed steps run without per-pass events (lds_set_pass_profiling stays off)
+    lds.set_pass_profiling(False)
+    times, fw_ms, updates, phase = [], [], [], []
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -259,19 +379,26 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            pass_us.append(t["pass_us"])
             fw_ms.append(t["fw_ms"])
             updates.append(t["stats"]["fw_edge_updates"])
             phase.append(t["stats"])
-            last_timing = t
             flush.zero_()
         torch.cuda.synchronize()
     launches = lds.launch_count() - launches0
-    lds.set_pass_profiling(False)
     if world > 1:
         torch.distributed.barrier()
     m = m_holder["m"]
     value, total_ms, units = job_rate(sum(times), sum(updates), dev)
+
+    # roofline of the pass kernel: one more first-round FW on the same input, untimed
+    # as a step, with a CUDA event pair around every pass launch on the handle's stream
+    lds.set_pass_profiling(True)
+    g = lds.Graph(n, ta, tb, stream=sptr)
+    g.fw(args.iters, density=args.density, precision=args.precision, want=())
+    pass_timing = g.fw_timing()
+    g.close()
+    lds.set_pass_profiling(False)
+    flush.zero_()
 
     # end to end through the C-ABI with host (pinned) buffers
     ha = torch.from_numpy(a).pin_memory()
@@ -282,10 +409,10 @@ def run_ours(args):
         t0 = time.perf_counter()
         g = lds.Graph(n, ha.numpy(), hb.numpy(), stream=sptr)
         if args.fw_only:
-            g.fw(args.iters, precision=args.precision, want=("r",))
-            e2e_updates = g.m * args.iters
+            g.fw(args.iters, density=args.density, precision=args.precision, want=("r",))
+            e2e_updates = m_holder["units"] * args.iters
         else:
-            g.topk(args.k, "edge", args.iters, args.precision)
+            g.topk(args.k, args.density, args.iters, args.precision)
             e2e_updates = lds.topk_last_stats()["fw_edge_updates"]
         g.close()
         dt = time.perf_counter() - t0
@@ -294,30 +421,49 @@ def run_ours(args):
         flush.zero_()
     e2e_value = e2e_updates / statistics.mean(e2e_times) if e2e_times else None
 
-    # the plain single-graph binary64 GPU path (Alg. 1 literally) on the same query
-    plain = None
+    plain = precision = answer = None
+    if not args.fw_only and rank == 0 and args.workload == "chung_lu_1m":
+        want = _golden_sets("chung_lu_1m_top10.txt")
+        got = [(str(d), tuple(int(x) for x in c)) for d, c in m_holder["result"]]
+        answer = {"golden": "tests/golden/chung_lu_1m_top10.txt (oracle.ldscvx, exact)",
+                  "matches_oracle": None if want is None else got == want[:args.k]}
     if not args.fw_only and not args.no_plain:
+        # the plain single-graph binary64 GPU path (Alg. 1 literally) on the same query
         pt = []
         for k in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g = lds.Graph(n, ta, tb, stream=sptr)
-            g.topk(args.k, "edge", args.iters, "fp64")
+            res64 = g.topk(args.k, args.density, args.iters, "fp64")
             g.close()
             torch.cuda.synchronize()
             if k:
                 pt.append(time.perf_counter() - t0)
             flush.zero_()
         plain = {"precision": "fp64 (Alg. 1 literal, symmetric slots)", "queries_per_s": 1.0 / statistics.mean(pt),
-                 "ms_per_query": 1000.0 * statistics.mean(pt)}
+                 "ms_per_query": 1000.0 * statistics.mean(pt), "same_output": _sets(res64) == _sets(m_holder["result"])}
+    if not args.fw_only and not args.no_precision and args.workload == "chung_lu_1m":
+        precision = precision_pattern(args, lds, n, ta, tb, sptr, flush, m_holder["result"])
 
     hbm, peak_kind = _peaks()
-    # algorithmic bytes of one pass: 16 B per edge in EXACT and FP32 (8 B of ids, 8 B of
-    # alpha read-modify-write), 24 B in FP64; the kernel itself moves fewer (kernel_bytes)
-    per_edge = {"exact": 16, "fp32": 16, "fp64": 24}[args.precision]
-    bytes_per_pass = per_edge * m
-    avg_pass_us = statistics.mean(pass_us)
+    # algorithmic bytes of one pass: per edge 16 B in EXACT and FP32 (8 B of ids, 8 B of
+    # alpha read-modify-write) and 24 B in FP64; per triangle 28 B (12 B of ids, two
+    # stored alphas read and written) and 44 B in FP64.  The kernels themselves move
+    # fewer (kernel_bytes): one choice bit per unit instead of alpha
+    tri = args.density == "triangle"
+    units = m_holder["units"]
+    per_unit = ({"exact": 28, "fp32": 28, "fp64": 44} if tri else {"exact": 16, "fp32": 16, "fp64": 24})[args.precision]
+    bytes_per_pass = per_unit * units
+    fused = pass_timing["pass_kernel"] == "fw_coop32_kernel"
+    if fused:
+        # the cooperative kernel runs whole iterations: the pass and the vertex
+        # update (16 B per vertex), timed per launch and divided by the iterations
+        bytes_per_pass += 16 * n
+    avg_pass_us = pass_timing["pass_us"]
     achieved = bytes_per_pass / (avg_pass_us * 1e-6) / 1e9
+    # one whole iteration: the pass plus the vertex update (16 B per vertex)
+    iter_us = 1000.0 * pass_timing["fw_ms"] / args.iters
+    iter_bytes = bytes_per_pass + 16 * n
     clocks = clk.summary()
     lat = sorted(times)
 
@@ -325,36 +471,97 @@ def run_ours(args):
         return lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC_TRI if tri else METRIC, "value": value, "unit": UNIT_TRI if tri else UNIT,
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"exact": "int64", "fp32": "f32", "fp64": "f64"}[args.precision],
             "data": "synthetic", "config": _config(args, n, m),
-            "fw_only": {"value": m * args.iters / (statistics.mean(fw_ms) / 1000.0), "unit": UNIT,
+            "fw_only": {"value": units * args.iters / (statistics.mean(fw_ms) / 1000.0),
+                        "unit": UNIT_TRI if tri else UNIT,
                         "fw_ms": statistics.mean(fw_ms), "note": "first-round FW kernels on G only"},
             "queries_per_s": None if args.fw_only else 1000.0 * args.steps / total_ms,
             "latency_ms": {"p50": pct(0.5), "p99": pct(0.99), "n": len(lat)},
             "plain_fp64_gpu": plain,
+            "precision_pattern": precision,
+            "answer": answer,
             "phases_ms": None if args.fw_only else {k: statistics.mean(p[k] for p in phase)
                                                      for k in ("ms_total", "ms_fw", "ms_extract", "ms_prune",
                                                                "ms_verify")},
             "result": None if args.fw_only else [[str(d), len(c)] for d, c in m_holder["result"]],
-            "roofline": {"bound": "hbm", "kernel": last_timing["pass_kernel"], "achieved": achieved, "peak": hbm,
+            "roofline": {"bound": "hbm", "kernel": pass_timing["pass_kernel"], "achieved": achieved, "peak": hbm,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": PASS_TRAFFIC.get((last_timing["pass_kernel"], args.precision)),
-                         "algorithmic_bytes_per_launch": bytes_per_pass, "bytes_per_edge": per_edge,
-                         "kernel_bytes_per_launch": last_timing["pass_bytes"], "avg_launch_us": avg_pass_us,
-                         "launches_timed": len(pass_us)},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * 4 * len(a)),
+                         "traffic": _traffic(pass_timing["pass_kernel"], args.precision),
+                         "algorithmic_bytes_per_launch": bytes_per_pass,
+                         ("bytes_per_triangle" if tri else "bytes_per_edge"): per_unit, "units_per_launch": units,
+                         "kernel_bytes_per_launch": pass_timing["pass_bytes"], "avg_launch_us": avg_pass_us,
+                         "launches_timed": pass_timing["pass_launches"],
+                         "timed": ("CUDA events around every launch of one extra first-round FW run (outside "
+                                   "the headline steps); " + ("each launch runs many whole iterations (pass + "
+                                   "vertex update), the figures are per iteration" if fused else
+                                   "one launch per pass")),
+                         "iteration": {"us": iter_us, "algorithmic_bytes": iter_bytes,
+                                       "frac": iter_bytes / (iter_us * 1e-6) / 1e9 / hbm,
+                                       "note": "whole FW iteration: pass + vertex update (+ folds), "
+                                               f"{per_unit} B/{'triangle' if tri else 'edge'} + 16 B/vertex"}},
+            "e2e": {"value": e2e_value, "unit": UNIT_TRI if tri else UNIT, "h2d_bytes_per_step": int(2 * 4 * len(a)),
                     "d2h_bytes_per_step": int(8 * n)},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(n, u, v)
+            line["cpu_baseline"] = cpu_baseline(n, u, v) if not tri else cpu_baseline_tri(n, u, v)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def precision_pattern(args, lds, n, ta, tb, sptr, flush, exact_result):
+    """The binary32 form on the same query: its time and answer, and the error of
+    its r vector after `iters` iterations against the binary64 oracle (Alg. 1
+    carried literally in binary64) on the oracle's vertex sample."""
+    import torch
+    qt = []
+    for k in range(3):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        g = lds.Graph(n, ta, tb, stream=sptr)
+        e0.record(torch.cuda.current_stream())
+        res32 = g.topk(args.k, "edge", args.iters, "fp32")
+        e1.record(torch.cuda.current_stream())
+        e1.synchronize()
+        g.close()
+        if k:
+            qt.append(e0.elapsed_time(e1))
+        flush.zero_()
+    out = {"fp32_query_ms": statistics.mean(qt), "fp32_same_sets_as_exact": _sets(res32) == _sets(exact_result)}
+    sample = _fw_sample("chung_lu_1m_fw500_sample.txt")
+    if sample is None or args.iters != 500:
+        out["r_error"] = None
+        return out
+    ids, Rq, r64 = sample
+    with lds.Graph(n, ta, tb, stream=sptr) as g:
+        ex = g.fw(args.iters, precision="exact", want=("R",))
+        f32 = g.fw(args.iters, precision="fp32", want=("r",))
+        f64 = g.fw(args.iters, precision="fp64", want=("r",))
+    Dn = ex["D"]
+    exact_r = np.array([float(q) / Dn for q in Rq])
+
+    def rel(a):
+        return float(np.max(np.abs(a - r64) / np.maximum(np.abs(r64), 1e-300)))
+    out["r_error"] = {
+        "sample": f"{len(ids)} vertices (2,000 seeded + the 48 highest-degree), oracle values from "
+                  "tests/golden/make_fw_sample.py",
+        "exact_R_bit_exact": [int(x) for x in ex["R"][ids]] == Rq,
+        "fp64_max_rel_err_vs_fp64_oracle": rel(f64["r"][ids]),
+        "fp32_max_rel_err_vs_fp64_oracle": rel(f32["r"][ids]),
+        "exact_max_rel_err_vs_fp64_oracle": rel(exact_r),
+        "note": "free-running forms: one tie decided differently forks the trajectory, so the FP32 error "
+                "is stated, not gated (the FP32 rounding itself is checked bit for bit against the oracle's "
+                "binary32 form in tests/test_gpu_core.py)",
+    }
+    return out
 
 
 def _sets(res):
@@ -407,6 +614,9 @@ def run_batch(args):
                    "graphs": len(queries), "triangle_queries": sum(q[2] == "triangle" for q in queries),
                    "k": 3, "iters": "100 edge / 200 triangle", "precision": "fp32", "workers": workers,
                    "generation_s": gen_s},
+        "autotuned": {"workers": workers,
+                      "fw_threads_per_graph": {f"nact<2^{b}": lds.fw_batch_threads((1 << b) - 1)
+                                               for b in range(6, 16)}},
         "plain_fp64_gpu": {"queries_per_s": sample / plain_s, "sample": sample, "same_output": same},
         "serial_fp32_gpu": {"queries_per_s": sample / serial_s, "sample": sample, "same_output": same_serial},
         "gpu_launches": int(launches), "clocks": clk.summary(),
@@ -508,14 +718,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--iters", type=int, default=500)
-    ap.add_argument("--precision", choices=["exact", "fp32", "fp64"], default="exact")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="chung_lu_1m")
+    ap.add_argument("--density", choices=["edge", "triangle"], default=None, help="default: the workload's")
+    ap.add_argument("--iters", type=int, default=None, help="default: the workload's (500 / 300)")
+    ap.add_argument("--precision", choices=["exact", "fp32", "fp64"], default=None)
     ap.add_argument("--ref-iters", type=int, default=3)
-    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--k", type=int, default=None)
     ap.add_argument("--fw-only", action="store_true", help="time ingest + FW only (profiling runs)")
     ap.add_argument("--no-plain", action="store_true", help="skip the binary64 comparison queries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the binary32 precision-pattern leg")
     ap.add_argument("--mode", choices=["query", "batch", "serve"], default="query",
                     help="query: the headline line; batch / serve: the many-query layers")
     ap.add_argument("--graphs", type=int, default=4096, help="batch mode: number of graphs")
@@ -527,6 +740,10 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--no-sweep", action="store_true", help="serve mode: skip the offered-load sweep")
     args = ap.parse_args()
+    spec = WORKLOADS[args.workload]
+    for key in ("density", "iters", "precision", "k"):
+        if getattr(args, key) is None:
+            setattr(args, key, spec[key])
     if args.mode == "batch" and args.impl == "ours":
         run_batch(args)
         return

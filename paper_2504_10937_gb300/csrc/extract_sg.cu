@@ -25,6 +25,7 @@
 // 5. Accepted groups give lo = min_S R', hi = max_S R' (over the denominator D);
 //    by Lemma 4 / Lemma 8 lo <= D phi(u) <= hi for u in the group.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdio>
 #include <cstdlib>
@@ -670,6 +671,7 @@ struct Chain {
 
 void extract_sg(lds_graph* g, SgState& st) {
     LDS_REQUIRE(g->fw_valid, LDS_EINVAL, "extract_sg: run lds_fw on this graph first");
+    const auto t_start = std::chrono::steady_clock::now();
     cudaStream_t s = g->stream;
     const int blk = 256;
     const int32_t n = g->n;
@@ -731,6 +733,7 @@ void extract_sg(lds_graph* g, SgState& st) {
     st.cuts.resize(ncut);
     LDS_CUDA(cudaMemcpyAsync(st.cuts.data(), dcuts.get(), ncut * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
+    const double ms_cuts = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     // 4. checks: every candidate alone first, then the merged segments of failures
     std::vector<int64_t> ca, cb;
     int64_t prev = 0;
@@ -793,8 +796,9 @@ void extract_sg(lds_graph* g, SgState& st) {
     }
     const char* vb = getenv("LDS_VERBOSE");
     if (vb && vb[0] == '1')
-        fprintf(stderr, "[extract_sg] n=%d candidates=%zu groups=%zu chain_checks=%lld\n", n, ca.size(),
-                st.group_end.size(), (long long)st.chain_checks);
+        fprintf(stderr, "[extract_sg] n=%d candidates=%zu groups=%zu chain_checks=%lld; sort+cuts %.2f ms, checks %.2f ms\n",
+                n, ca.size(), st.group_end.size(), (long long)st.chain_checks, ms_cuts,
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count() - ms_cuts);
 }
 
 }  // namespace lds

@@ -197,7 +197,12 @@ __global__ void u8_count_kernel(const uint8_t* f, int64_t k, int32_t* cnt) {
 
 struct Timers {
     double fw = 0, sg = 0, prune = 0, verify = 0, refine = 0, total = 0;
+    double init = 0, comps = 0, sub = 0, sub_init = 0;     // host-clock split of the rest
 };
+
+static double ms_since(std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+}
 
 struct Driver {
     lds_graph* G;
@@ -460,7 +465,12 @@ void Driver::run() {
     auto elapsed = [&] { return std::chrono::duration<double>(std::chrono::steady_clock::now() - T0).count(); };
     cudaStream_t s = st();
     if (tri) ensure_triangles(G);
-    init_bounds(G, bG);
+    {
+        auto ti = std::chrono::steady_clock::now();
+        init_bounds(G, bG);
+        LDS_CUDA(cudaStreamSynchronize(s));
+        tm.init += ms_since(ti);
+    }
     if (verbose) fprintf(stderr, "[lds_topk] initial bounds at %.3fs\n", elapsed());
     DevBuf<int32_t> members;
     std::vector<int64_t> offs;
@@ -513,6 +523,7 @@ void Driver::run() {
         std::vector<int32_t> cs;
         auto tv0 = std::chrono::steady_clock::now();
         components(G, sorted.get(), ssz, sc, cm, cs);
+        tm.comps += ms_since(tv0);
         if (verbose)
             fprintf(stderr, "[lds_topk]   %zu components in %.1f ms\n", cs.size() - 1,
                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv0).count());
@@ -558,10 +569,15 @@ void Driver::run() {
             int32_t n_try = N;
             while (true) {
                 ++stats.refined;
+                auto ts = std::chrono::steady_clock::now();
                 lds_graph* h = subgraph(G, comp, csize, sc);
                 struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+                tm.sub += ms_since(ts);
+                ts = std::chrono::steady_clock::now();
                 Bounds bs;
                 init_bounds(h, bs);
+                LDS_CUDA(cudaStreamSynchronize(s));
+                tm.sub_init += ms_since(ts);
                 if (h->n)
                     LDS_LAUNCH(sub_bounds_kernel, grid_for(h->n, DB), DB, 0, s, h->to_orig.get(), comp, h->n,
                                bG.un.get(), bG.ud.get(), bs.un.get(), bs.ud.get());
@@ -600,6 +616,11 @@ void Driver::run() {
     stats.flows = vst.flows;
     stats.denser_neighbour = vst.denser_neighbour;
     tm.total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - T0).count();
+    if (verbose)
+        fprintf(stderr,
+                "[lds_topk] total %.1f ms: fw %.1f, extract %.1f, prune %.1f, verify %.1f, initial bounds %.1f, "
+                "components %.1f, subgraph handles %.1f, their bounds %.1f\n",
+                tm.total, tm.fw, tm.sg, tm.prune, tm.verify, tm.init, tm.comps, tm.sub, tm.sub_init);
     stats.ms_total = tm.total;
     stats.ms_fw = tm.fw;
     stats.ms_extract = tm.sg;
