@@ -247,6 +247,21 @@ def fw_tri_fp64_literal(n: int, tris, N: int, record=None):
     return r, a
 
 
+def snap_tri_weights(alpha, Dn3: int):
+    """An exactly feasible integer solution W (|T|, 3) over the denominator Dn3
+    from binary64 alphas (the snapping of the Def. 12 check's reading): every
+    weight is rint(alpha * Dn3) except that the member with the largest alpha
+    (the first one on ties) takes Dn3 minus the other two, so every row sums to
+    Dn3 and no weight is negative."""
+    a = np.asarray(alpha, dtype=np.float64).reshape(-1, 3)
+    W = np.rint(a * float(Dn3)).astype(np.int64)
+    if len(a):
+        j = np.argmax(a, axis=1)
+        rows = np.arange(len(a))
+        W[rows, j] = Dn3 - (W.sum(axis=1) - W[rows, j])
+    return W
+
+
 # --------------------------------------------------------------------------
 # binary32, recurrence form (alpha rebuilt exactly from the choices)
 # --------------------------------------------------------------------------

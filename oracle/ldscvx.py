@@ -71,7 +71,7 @@ def _run_fw(g: _Graph, verts, N, precision):
         elif precision == "fp64":
             _, a = fw.fw_tri_fp64_literal(g.n, t, N)
             Dn = 3 * fw.D(N)
-            W = np.rint(a * Dn).astype(np.int64)
+            W = fw.snap_tri_weights(a, Dn)
         else:
             _, W, Dn, _ = fw.fw_tri_exact(g.n, t, N)
         return t, W, Dn

@@ -197,3 +197,17 @@ def test_fp32_weights_are_feasible():
     assert R.sum() == len(u) * Dn
     # binary32 loads track the exact loads of the same choices
     assert np.allclose(r32, R / Dn, rtol=2e-5, atol=2e-5)
+
+
+def test_snapped_triangle_weights_are_feasible():
+    # the binary64 alphas snapped to integers: every row sums to exactly 3 D,
+    # no weight is negative, and each is within one unit of alpha * 3 D
+    n, u, v = random_graph(12, 0.6, seed=23)
+    tris = graph.triangles(n, u, v)
+    for N in (1, 7, 30):
+        _, a = fw.fw_tri_fp64_literal(n, tris, N)
+        Dn3 = 3 * fw.D(N)
+        W = fw.snap_tri_weights(a, Dn3)
+        assert np.all(W.sum(axis=1) == Dn3)
+        assert W.min() >= 0
+        assert np.abs(W - a * Dn3).max() <= 1.5
