@@ -347,3 +347,61 @@ def workload_rmat20(seed: int = 3, scale: int = 20):
     """R-MAT scale 20, edge factor 16, (a, b, c) = (0.57, 0.19, 0.19), plus 20
     near-cliques of size 30-200 at probability 0.8."""
     return rmat(scale, 16, 0.57, 0.19, 0.19, seed, n_cliques=20)
+
+
+# --- device-side generation of the large R-MAT graph -------------------------
+
+def _splitmix_torch(seed: int, first: int, k: int, device):
+    """Outputs first+1 .. first+k of SplitMix64(seed) as int64 torch tensors on
+    `device`, bit for bit equal to SplitMix64.u64 (int64 products wrap like
+    uint64 ones; right shifts are made logical by masking)."""
+    import torch
+
+    def s64(x):            # an unsigned 64-bit constant as the int64 with the same bits
+        x &= _MASK64
+        return x - (1 << 64) if x >= (1 << 63) else x
+
+    def lsr(z, r):
+        return (z >> r) & ((1 << (64 - r)) - 1)
+
+    idx = torch.arange(first + 1, first + k + 1, dtype=torch.int64, device=device)
+    z = idx * s64(int(_GOLDEN)) + s64(int(seed))
+    z = (z ^ lsr(z, 30)) * s64(int(_MIX1))
+    z = (z ^ lsr(z, 27)) * s64(int(_MIX2))
+    return z ^ lsr(z, 31)
+
+
+def rmat_device(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int, device="cuda"):
+    """The samples and the random relabelling of ``rmat(scale, edge_factor, a,
+    b, c, seed)`` without planted near-cliques, drawn on a CUDA device with
+    torch: SplitMix64 outputs, quadrant choices and the permutation are the
+    same numbers the numpy generator draws.  Returns ``(n, src, dst)`` as int32
+    device tensors in raw form (repeats, both orientations and self-loops left
+    in): ``lds_create_graph`` canonicalises them to the graph ``rmat`` returns.
+    Used for sizes whose numpy generation takes many minutes (scale 24)."""
+    import torch
+    n = 1 << scale
+    samples = edge_factor * n
+    src = torch.zeros(samples, dtype=torch.int64, device=device)
+    dst = torch.zeros(samples, dtype=torch.int64, device=device)
+    ab, abc = a + b, a + b + c
+    counter = 0
+    chunk = 1 << 26
+    for level in range(scale):
+        bit = 1 << (scale - 1 - level)
+        for lo in range(0, samples, chunk):
+            k = min(chunk, samples - lo)
+            z = _splitmix_torch(seed, counter + lo, k, device)
+            x = ((z >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+            right = ((x >= a) & (x < ab)) | (x >= abc)
+            down = x >= ab
+            src[lo:lo + k] += down.to(torch.int64) * bit
+            dst[lo:lo + k] += right.to(torch.int64) * bit
+            del z, x, right, down
+        counter += samples
+    counter += n                                   # the near-clique vertex permutation (unused here)
+    keys = _splitmix_torch(seed, counter, n, device) ^ (-(1 << 63))    # unsigned order as signed order
+    perm = torch.argsort(keys, stable=True)
+    del keys
+    # relabel as rmat does: old id x becomes perm[x]
+    return n, perm[src].to(torch.int32), perm[dst].to(torch.int32)

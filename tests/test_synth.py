@@ -75,3 +75,16 @@ def test_scramble_keeps_the_edge_set():
     assert np.array_equal(got, u.astype(np.int64) * n + v)
     assert np.any(a == b)                   # self-loops are present
     assert len(a) > len(u)                  # and repeats
+
+
+def test_rmat_device_reproduces_rmat():
+    # the device-side R-MAT (used for scale 24) draws the same SplitMix64 numbers,
+    # quadrants and relabelling as the numpy generator; run here on the CPU
+    pytest = __import__("pytest")
+    torch = pytest.importorskip("torch")
+    for scale, seed in ((8, 77), (11, 5)):
+        n, u, v, _ = synth.rmat(scale, 16, 0.57, 0.19, 0.19, seed=seed, n_cliques=0)
+        n2, s, d = synth.rmat_device(scale, 16, 0.57, 0.19, 0.19, seed=seed, device="cpu")
+        assert n2 == n and s.dtype == torch.int32
+        cu, cv = synth._canon(n2, s.numpy(), d.numpy())
+        assert np.array_equal(cu, u) and np.array_equal(cv, v)
