@@ -480,13 +480,100 @@ static void run_edge_fw(lds_graph* g, int N, lds_precision p, EdgeFwState& st, P
 
 // ---------------------------------------------------------------- triangle FW
 
+// ---- Alg. 6 literally in binary64: one alpha per (vertex, triangle) pair,
+// alpha <- (1 - gamma) alpha + gamma alpha_hat with every operation rounded on
+// its own (no fused multiply-add), and r_v summed left to right over v's
+// triangles in ascending triangle order, starting from 0.
+
+__global__ void tri_alpha_init64_kernel(double* alpha, int64_t n3) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += stride) alpha[i] = 1.0 / 3.0;
+}
+
+__global__ void tri_rsum64_kernel(const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta, const int32_t* tb,
+                                  const double* alpha, int32_t nact, double* r) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nact; v += stride) {
+        double acc = 0.0;
+        for (int64_t q = vt_ptr[v]; q < vt_ptr[v + 1]; ++q) {
+            const int32_t t = vt_idx[q];
+            const int k = ta[t] == v ? 0 : (tb[t] == v ? 1 : 2);
+            acc = __dadd_rn(acc, alpha[3 * (int64_t)t + k]);
+        }
+        r[v] = acc;
+    }
+}
+
+// receiving column: the lowest load, ties to the later column (the larger id)
+__global__ void tri_pass64_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
+                                  const double* r, double gam, double om, double* alpha, uint8_t* last) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        const double ra = r[ta[t]], rb = r[tb[t]], rc = r[tc[t]];
+        int best = 2;
+        double bv = rc;
+        if (rb < bv) { best = 1; bv = rb; }
+        if (ra < bv) best = 0;
+        for (int k = 0; k < 3; ++k)
+            alpha[3 * t + k] = __dadd_rn(__dmul_rn(om, alpha[3 * t + k]), __dmul_rn(gam, k == best ? 1.0 : 0.0));
+        if (last) last[t] = (uint8_t)best;
+    }
+}
+
+// an exactly feasible integer solution: every weight rint(alpha D), except that the
+// member with the largest alpha (the first on ties) takes D minus the other two
+__global__ void tri_w_from_alpha64_kernel(const double* alpha, int64_t ntri, int64_t Dn3, uint32_t* W) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
+        int64_t w[3];
+        int j = 0;
+        for (int k = 0; k < 3; ++k) {
+            w[k] = llrint(__dmul_rn(alpha[3 * t + k], (double)Dn3));
+            if (alpha[3 * t + k] > alpha[3 * t + j]) j = k;
+        }
+        w[j] = Dn3 - (w[0] + w[1] + w[2] - w[j]);
+        for (int k = 0; k < 3; ++k) W[3 * t + k] = (uint32_t)w[k];
+    }
+}
+
 struct TriFwState {
     DevBuf<int64_t> R;
     DevBuf<float> r32;
+    DevBuf<double> r64;        // binary64 form
+    DevBuf<uint8_t> last64;    // binary64 form: receiving column of the last iteration
     DevBuf<uint32_t> W;        // [3 ntri]
     DevBuf<uint32_t> planes;   // 2 planes per stored iteration
     int64_t last_pair = -1;
 };
+
+static void run_tri_fw64(lds_graph* g, int N, TriFwState& st, PassTimer& timer) {
+    cudaStream_t s = g->stream;
+    const int64_t ntri = g->ntri;
+    const int32_t nact = g->nact;
+    const int blk = 256;
+    ensure_vertex_triangles(g);
+    DevBuf<double> alpha(std::max<int64_t>(3 * ntri, 1), s);
+    st.r64.alloc(std::max<int32_t>(nact, 1), s);
+    st.last64.alloc(std::max<int64_t>(ntri, 1), s);
+    st.W.alloc(std::max<int64_t>(3 * ntri, 1), s);
+    if (ntri) LDS_LAUNCH(tri_alpha_init64_kernel, grid_for(3 * ntri, blk), blk, 0, s, alpha.get(), 3 * ntri);
+    if (ntri) LDS_CUDA(cudaMemsetAsync(st.last64.get(), 2, ntri, s));
+    if (nact)
+        LDS_LAUNCH(tri_rsum64_kernel, grid_for(nact, blk), blk, 0, s, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(),
+                   g->tb.get(), alpha.get(), nact, st.r64.get());
+    for (int i = 1; i <= N && ntri; ++i) {
+        const double gam = 2.0 / (double)(i + 2);
+        const double om = 1.0 - gam;
+        timer.start(s);
+        LDS_LAUNCH(tri_pass64_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
+                   st.r64.get(), gam, om, alpha.get(), i == N ? st.last64.get() : (uint8_t*)nullptr);
+        timer.stop(s);
+        LDS_LAUNCH(tri_rsum64_kernel, grid_for(nact, blk), blk, 0, s, g->vt_ptr.get(), g->vt_idx.get(), g->ta.get(),
+                   g->tb.get(), alpha.get(), nact, st.r64.get());
+    }
+    const int64_t Dn3 = 3 * (int64_t)(N + 1) * (N + 2);
+    if (ntri) LDS_LAUNCH(tri_w_from_alpha64_kernel, grid_for(ntri, blk), blk, 0, s, alpha.get(), ntri, Dn3, st.W.get());
+}
 
 static void run_tri_fw(lds_graph* g, int N, lds_precision p, TriFwState& st, PassTimer& timer) {
     cudaStream_t s = g->stream;
@@ -623,10 +710,16 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
         ensure_triangles(g);
         TriFwState st;
         LDS_CUDA(cudaEventRecord(e0, s));
-        run_tri_fw(g, iters, p, st, timer);
+        if (p == LDS_FP64) run_tri_fw64(g, iters, st, timer);
+        else run_tri_fw(g, iters, p, st, timer);
         LDS_CUDA(cudaEventRecord(e1, s));
-        g->pass_kernel = "fw_tri_pass_kernel";
-        g->pass_bytes = 12 * g->ntri + 8 * ((g->ntri + 31) / 32) + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
+        if (p == LDS_FP64) {
+            g->pass_kernel = "tri_pass64_kernel";
+            g->pass_bytes = 12 * g->ntri + 48 * g->ntri + 24 * (int64_t)nact;
+        } else {
+            g->pass_kernel = "fw_tri_pass_kernel";
+            g->pass_bytes = 12 * g->ntri + 8 * ((g->ntri + 31) / 32) + (p == LDS_EXACT ? 8 : 4) * (int64_t)nact;
+        }
         const int64_t ntri = g->ntri;
         LDS_CUDA(cudaMemsetAsync(R_int.get(), 0, std::max(n, 1) * sizeof(int64_t), s));
         if (ntri)
@@ -635,6 +728,8 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
         if (n) {
             if (p == LDS_EXACT)
                 LDS_LAUNCH(loads_to_double_kernel<int64_t>, grid_for(n, blk), blk, 0, s, st.R.get(), nact, n, (double)Dn, r_int.get());
+            else if (p == LDS_FP64)
+                LDS_LAUNCH(loads_to_double_kernel<double>, grid_for(n, blk), blk, 0, s, st.r64.get(), nact, n, 1.0, r_int.get());
             else
                 LDS_LAUNCH(loads_to_double_kernel<float>, grid_for(n, blk), blk, 0, s, st.r32.get(), nact, n, 1.0, r_int.get());
         }
@@ -645,7 +740,9 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
             int64_t nch = (ntri + 31) / 32;
             const uint32_t* p0 = st.planes.get() + 2 * std::max<int64_t>(st.last_pair, 0) * nch;
             if (ntri) {
-                if (iters == 0) LDS_CUDA(cudaMemsetAsync(g->fw_last.get(), 2, ntri, s));
+                if (p == LDS_FP64)
+                    LDS_CUDA(cudaMemcpyAsync(g->fw_last.get(), st.last64.get(), ntri, cudaMemcpyDeviceToDevice, s));
+                else if (iters == 0) LDS_CUDA(cudaMemsetAsync(g->fw_last.get(), 2, ntri, s));
                 else LDS_LAUNCH(tri_last_kernel, grid_for(ntri, blk), blk, 0, s, p0, p0 + nch, ntri, g->fw_last.get());
             }
         }

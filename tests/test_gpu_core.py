@@ -181,6 +181,13 @@ def test_fw_triangle_exact_and_fp32(lds, N):
         r32, W32, _ = ofw.fw_tri_fp32(n, tris, N)
         assert np.array_equal(got32["r"], r32.astype(np.float64))
         assert np.array_equal(got32["W"], W32)
+        # Alg. 6 literally in binary64 (one alpha per vertex-triangle pair, r summed
+        # in ascending triangle order): bit for bit, hence within the 1e-6 bound
+        with lds.Graph(n, u, v) as g:
+            got64 = g.fw(N, density="triangle", precision="fp64", want=("r", "W"))
+        r64, a64 = ofw.fw_tri_fp64_literal(n, tris, N)
+        assert np.array_equal(got64["r"], r64)
+        assert np.array_equal(got64["W"], ofw.snap_tri_weights(a64, Dn3))
 
 
 def test_core_numbers(lds):
