@@ -336,6 +336,46 @@ __device__ __forceinline__ void pattern_delta(int k, const int64_t* pp, const in
     d[tgt] += moved;
 }
 
+// incidence r of the vertex at position p: if the pattern's member of largest
+// position in (b0, b1] is p, add its (new - old) change of the loads to delta
+__device__ __forceinline__ void chain_incidence(bool tri, int64_t p, int64_t r, const int32_t* order,
+                                                const int32_t* pos, int64_t a, int64_t b0, int64_t b1,
+                                                const int64_t* rowptr, const int32_t* col, const int64_t* slot_edge,
+                                                const int32_t* eu, const int64_t* vt_ptr, const int32_t* vt_idx,
+                                                const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                                const int64_t* W, int64_t Dn, unsigned long long* delta) {
+    const int32_t x = order[p];
+    int k;
+    int64_t pp[3], w[3];
+    if (tri) {
+        const int32_t t = vt_idx[vt_ptr[x] + r];
+        const int32_t v[3] = {ta[t], tb[t], tc[t]};
+        k = 3;
+        for (int j = 0; j < 3; ++j) {
+            pp[j] = pos[v[j]];
+            w[j] = W[3 * (int64_t)t + j];
+        }
+    } else {
+        const int64_t q = rowptr[x] + r;
+        const int32_t y = col[q];
+        const int64_t ed = slot_edge[q];
+        k = 2;
+        pp[0] = p;
+        pp[1] = pos[y];
+        w[0] = (eu[ed] == x) ? W[ed] : Dn - W[ed];
+        w[1] = Dn - w[0];
+    }
+    int64_t best = -1;
+    for (int j = 0; j < k; ++j)
+        if (pp[j] > b0 && pp[j] <= b1 && pp[j] > best) best = pp[j];
+    if (best != p) return;
+    int64_t dn[3], dold[3];
+    pattern_delta(k, pp, w, a, b1, dn);
+    pattern_delta(k, pp, w, a, b0, dold);
+    for (int j = 0; j < k; ++j)
+        if (dn[j] != dold[j]) atomicAdd(delta + pp[j], (unsigned long long)(dn[j] - dold[j]));
+}
+
 __global__ void chain_extend_kernel(bool tri, const int32_t* order, const int32_t* pos, int64_t a, int64_t b0,
                                     int64_t b1, const int64_t* ioff, int64_t ninc, const int64_t* rowptr,
                                     const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
@@ -346,38 +386,110 @@ __global__ void chain_extend_kernel(bool tri, const int32_t* order, const int32_
     const int32_t plo = (int32_t)(b0 + 1), phi = (int32_t)(b1 + 1);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ninc; i += stride) {
         const int64_t p = inc_position(ioff, plo, phi, i);
-        const int32_t x = order[p];
-        const int64_t r = i - ioff[p - plo];
-        int k;
-        int64_t pp[3], w[3];
-        if (tri) {
-            const int32_t t = vt_idx[vt_ptr[x] + r];
-            const int32_t v[3] = {ta[t], tb[t], tc[t]};
-            k = 3;
-            for (int j = 0; j < 3; ++j) {
-                pp[j] = pos[v[j]];
-                w[j] = W[3 * (int64_t)t + j];
-            }
+        chain_incidence(tri, p, i - ioff[p - plo], order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx,
+                        ta, tb, tc, W, Dn, delta);
+    }
+}
+
+// The whole walk of Alg. 2's merge loop in one CTA, for small graphs: candidate k
+// starting at the current start takes its single check (precomputed); any other
+// extends the chain of the current start (chain_incidence) and takes the block's
+// min / max over X, S and Z.  Writes the accepted groups' ends and bounds.
+__global__ void __launch_bounds__(1024) sg_walk_small_kernel(
+    bool tri, const int32_t* order, const int32_t* pos, int32_t n, int32_t nact, int32_t ncand, const int64_t* ca,
+    const int64_t* cb, const long long* mnS, const long long* mxS, const long long* mnX, const long long* mxZ,
+    const int64_t* R, const int64_t* rowptr, const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
+    const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+    const int64_t* W, int64_t Dn, unsigned long long* delta, int64_t* gend, long long* glo, long long* ghi,
+    int32_t* ngroups, int64_t* chain_checks) {
+    __shared__ unsigned long long red[4][32];
+    __shared__ long long res[4];
+    __shared__ int64_t s_start, s_a, s_b;
+    __shared__ int32_t s_ng, s_stop;
+    __shared__ int64_t s_checks;
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        s_start = 0;
+        s_a = -1;
+        s_b = -1;
+        s_ng = 0;
+        s_stop = 0;
+        s_checks = 0;
+    }
+    __syncthreads();
+    for (int32_t k = 0; k < ncand; ++k) {
+        const int64_t start = s_start;
+        long long lo, hi, mx, mz;
+        if (ca[k] == start) {
+            lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
-            const int64_t q = rowptr[x] + r;
-            const int32_t y = col[q];
-            const int64_t ed = slot_edge[q];
-            k = 2;
-            pp[0] = p;
-            pp[1] = pos[y];
-            w[0] = (eu[ed] == x) ? W[ed] : Dn - W[ed];
-            w[1] = Dn - w[0];
+            if (s_a != start) {
+                for (int32_t p = tid; p < n; p += bd) delta[p] = 0;
+                __syncthreads();
+                if (tid == 0) { s_a = start; s_b = start - 1; }
+                __syncthreads();
+            }
+            const int64_t b0 = s_b, b1 = cb[k];
+            // positions (b0, b1]: each one's incidences spread over the block
+            for (int64_t p = b0 + 1; p <= b1; ++p) {
+                const int32_t x = order[p];
+                if (x >= nact) continue;
+                const int64_t deg = tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
+                for (int64_t r = tid; r < deg; r += bd)
+                    chain_incidence(tri, p, r, order, pos, start, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx,
+                                    ta, tb, tc, W, Dn, delta);
+            }
+            __syncthreads();
+            unsigned long long e0 = ~0ull, e1 = 0, e2 = ~0ull, e3 = 0;
+            for (int32_t p = tid; p < n; p += bd) {
+                const unsigned long long v = (unsigned long long)(R[order[p]] + (int64_t)delta[p]);
+                if (p < start) e2 = min(e2, v);
+                else if (p <= b1) { e0 = min(e0, v); e1 = max(e1, v); }
+                else e3 = max(e3, v);
+            }
+            for (int o = 16; o; o >>= 1) {
+                e0 = min(e0, __shfl_xor_sync(0xffffffffu, e0, o));
+                e1 = max(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+                e2 = min(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+                e3 = max(e3, __shfl_xor_sync(0xffffffffu, e3, o));
+            }
+            if (lane == 0) { red[0][wid] = e0; red[1][wid] = e1; red[2][wid] = e2; red[3][wid] = e3; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int j = 1; j < (bd + 31) / 32; ++j) {
+                    e0 = min(e0, red[0][j]); e1 = max(e1, red[1][j]);
+                    e2 = min(e2, red[2][j]); e3 = max(e3, red[3][j]);
+                }
+                res[0] = (long long)e0;
+                res[1] = (long long)e1;
+                res[2] = e2 == ~0ull ? LLONG_MAX : (long long)e2;
+                res[3] = b1 == n - 1 ? LLONG_MIN : (long long)e3;
+                s_b = b1;
+                ++s_checks;
+            }
+            __syncthreads();
+            lo = res[0]; hi = res[1]; mx = res[2]; mz = res[3];
         }
-        // the pattern is handled by its member of largest position in (b0, b1]
-        int64_t best = -1;
-        for (int j = 0; j < k; ++j)
-            if (pp[j] > b0 && pp[j] <= b1 && pp[j] > best) best = pp[j];
-        if (best != p) continue;
-        int64_t dn[3], dold[3];
-        pattern_delta(k, pp, w, a, b1, dn);
-        pattern_delta(k, pp, w, a, b0, dold);
-        for (int j = 0; j < k; ++j)
-            if (dn[j] != dold[j]) atomicAdd(delta + pp[j], (unsigned long long)(dn[j] - dold[j]));
+        const bool xok = start == 0 || mx > hi;
+        const bool zok = cb[k] == n - 1 || mz < lo;
+        __syncthreads();
+        if (tid == 0) {
+            if (xok && zok) {
+                gend[s_ng] = cb[k] + 1;
+                glo[s_ng] = lo;
+                ghi[s_ng] = hi;
+                ++s_ng;
+                s_start = cb[k] + 1;
+            } else if (!xok) {
+                s_stop = 1;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+    }
+    if (tid == 0) {
+        *ngroups = s_ng;
+        *chain_checks = s_checks;
     }
 }
 
@@ -501,28 +613,29 @@ __global__ void u32_to_i32_kernel(const uint32_t* in, int64_t k, int32_t* out) {
 
 }  // namespace
 
-void ensure_vertex_triangles(lds_graph* g) {
-    if (g->vt_ptr.p) return;
-    ensure_triangles(g);
-    cudaStream_t s = g->stream;
-    const int32_t nact = g->nact;
-    const int64_t nt = g->ntri;
+void build_vertex_triangles(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t nt, int32_t nact,
+                            DevBuf<int64_t>& vt_ptr, DevBuf<int32_t>& vt_idx, cudaStream_t s) {
     const int blk = 256;
-    g->vt_ptr.alloc(nact + 1, s);
-    g->vt_idx.alloc(std::max<int64_t>(3 * nt, 1), s);
+    vt_ptr.alloc(nact + 1, s);
+    vt_idx.alloc(std::max<int64_t>(3 * nt, 1), s);
     if (nt == 0) {
-        LDS_CUDA(cudaMemsetAsync(g->vt_ptr.get(), 0, (nact + 1) * sizeof(int64_t), s));
+        LDS_CUDA(cudaMemsetAsync(vt_ptr.get(), 0, (nact + 1) * sizeof(int64_t), s));
         LDS_CUDA(cudaStreamSynchronize(s));
         return;
     }
     DevBuf<uint64_t> key(3 * nt, s);
     DevBuf<uint32_t> tid(3 * nt, s);
-    LDS_LAUNCH(vt_key_kernel, grid_for(3 * nt, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), nt, key.get(),
-               tid.get());
+    LDS_LAUNCH(vt_key_kernel, grid_for(3 * nt, blk), blk, 0, s, ta, tb, tc, nt, key.get(), tid.get());
     radix_sort_u64(key.get(), tid.get(), 3 * nt, bit_length_u64((uint64_t)nact), s);
-    LDS_LAUNCH(vt_ptr_kernel, grid_for(3 * nt, blk), blk, 0, s, key.get(), 3 * nt, nact, g->vt_ptr.get());
-    LDS_LAUNCH(u32_to_i32_kernel, grid_for(3 * nt, blk), blk, 0, s, tid.get(), 3 * nt, g->vt_idx.get());
+    LDS_LAUNCH(vt_ptr_kernel, grid_for(3 * nt, blk), blk, 0, s, key.get(), 3 * nt, nact, vt_ptr.get());
+    LDS_LAUNCH(u32_to_i32_kernel, grid_for(3 * nt, blk), blk, 0, s, tid.get(), 3 * nt, vt_idx.get());
     LDS_CUDA(cudaStreamSynchronize(s));
+}
+
+void ensure_vertex_triangles(lds_graph* g) {
+    if (g->vt_ptr.p) return;
+    ensure_triangles(g);
+    build_vertex_triangles(g->ta.get(), g->tb.get(), g->tc.get(), g->ntri, g->nact, g->vt_ptr, g->vt_idx, g->stream);
 }
 
 // Checks the given disjoint segments (positions, inclusive) and returns
@@ -609,6 +722,9 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
     LDS_CUDA(cudaMemcpyAsync(maxZ.data(), dmaxZ.get(), nseg * sizeof(long long), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
 }
+
+// graphs up to this many vertices run the check walk in one CTA (sg_walk_small_kernel)
+constexpr int32_t kSmallWalk = 65536;
 
 // A growing segment [a, b] of one chain of merged candidates (see chain_extend_kernel).
 struct Chain {
@@ -767,6 +883,53 @@ void extract_sg(lds_graph* g, SgState& st) {
     // For a fixed start, growing the segment only lowers the X vertices' modified
     // loads and only raises max_S r': once the X-side test fails it fails for
     // every longer merge, so the whole rest is the unaccepted remainder.
+    // Small graphs (refinement rounds on G[C]): every single check at once, then the
+    // whole walk, chains included, in one CTA.
+    if (n <= kSmallWalk && ncand > 0) {
+        ensure_checked(ncand - 1);
+        const bool tri_g = tri;
+        if (tri_g) ensure_vertex_triangles(g);
+        else if (g->m) ensure_slot_edge(g);
+        DevBuf<int64_t> dca(ncand, s), dcb(ncand, s), dgend(ncand, s), dchk(1, s);
+        DevBuf<long long> d1(ncand, s), d2(ncand, s), d3(ncand, s), d4(ncand, s), dlo(ncand, s), dhi(ncand, s);
+        DevBuf<unsigned long long> delta(n, s);
+        DevBuf<int32_t> dng(1, s);
+        copy_in(dca.get(), ca.data(), LDS_MEM_HOST, ncand * sizeof(int64_t), s);
+        copy_in(dcb.get(), cb.data(), LDS_MEM_HOST, ncand * sizeof(int64_t), s);
+        copy_in(d1.get(), mnS.data(), LDS_MEM_HOST, ncand * sizeof(long long), s);
+        copy_in(d2.get(), mxS.data(), LDS_MEM_HOST, ncand * sizeof(long long), s);
+        copy_in(d3.get(), mnX.data(), LDS_MEM_HOST, ncand * sizeof(long long), s);
+        copy_in(d4.get(), mxZ.data(), LDS_MEM_HOST, ncand * sizeof(long long), s);
+        LDS_LAUNCH(sg_walk_small_kernel, 1, 1024, 0, s, tri_g, st.order.get(), st.pos.get(), n, g->nact,
+                   (int32_t)ncand, dca.get(), dcb.get(), d1.get(), d2.get(), d3.get(), d4.get(), g->fw_R.get(),
+                   g->rowptr.get(), g->col.get(), tri_g ? nullptr : g->slot_edge.get(), g->eu.get(),
+                   tri_g ? g->vt_ptr.get() : nullptr, tri_g ? g->vt_idx.get() : nullptr, g->ta.get(), g->tb.get(),
+                   g->tc.get(), g->fw_W.get(), g->fw_D, delta.get(), dgend.get(), dlo.get(), dhi.get(), dng.get(),
+                   dchk.get());
+        int32_t ng = 0;
+        int64_t chk = 0;
+        LDS_CUDA(cudaMemcpyAsync(&ng, dng.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaMemcpyAsync(&chk, dchk.get(), sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        st.group_end.resize(ng);
+        st.lo.resize(ng);
+        st.hi.resize(ng);
+        if (ng) {
+            LDS_CUDA(cudaMemcpyAsync(st.group_end.data(), dgend.get(), ng * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaMemcpyAsync(st.lo.data(), dlo.get(), ng * sizeof(long long), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaMemcpyAsync(st.hi.data(), dhi.get(), ng * sizeof(long long), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+        }
+        st.chain_checks = chk;
+        const char* vb0 = getenv("LDS_VERBOSE");
+        if (vb0 && vb0[0] == '1')
+            fprintf(stderr, "[extract_sg] n=%d candidates=%zu groups=%zu chain_checks=%lld (one-CTA walk); "
+                            "sort+cuts %.2f ms, checks %.2f ms\n",
+                    n, ca.size(), st.group_end.size(), (long long)st.chain_checks, ms_cuts,
+                    std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count() -
+                        ms_cuts);
+        return;
+    }
     // Merged candidates of one start are checked incrementally (Chain): each step
     // only walks the patterns of the positions it adds.
     Chain chain(g, st);

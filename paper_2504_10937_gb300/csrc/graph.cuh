@@ -87,6 +87,9 @@ void ensure_fw_view(lds_graph* g);
 
 // Builds the vertex -> triangle incidence (ascending triangle order) if not present.
 void ensure_vertex_triangles(lds_graph* g);
+// The same incidence for any triangle list (vt_idx indexes that list).
+void build_vertex_triangles(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t nt, int32_t nact,
+                            DevBuf<int64_t>& vt_ptr, DevBuf<int32_t>& vt_idx, cudaStream_t s);
 
 // Core (tr-core) numbers of G[alive] (internal ids, -1 outside the mask).
 void core_numbers(lds_graph* g, bool tri, int64_t* core_int, const uint8_t* init_alive);

@@ -182,6 +182,25 @@ __global__ void alive_degree_kernel(const int64_t* rowptr, const int32_t* col, c
 }
 
 // triangle counts of G[alive]; triangles with a dead vertex are marked dead
+__global__ void tri_all_alive_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
+                                     const uint8_t* alive, int32_t* flag) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride)
+        flag[t] = alive[ta[t]] && alive[tb[t]] && alive[tc[t]];
+}
+
+__global__ void tri_compact_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
+                                   const int32_t* flag, const int64_t* tpos, int32_t* oa, int32_t* ob, int32_t* oc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride)
+        if (flag[t]) {
+            const int64_t o = tpos[t];
+            oa[o] = ta[t];
+            ob[o] = tb[t];
+            oc[o] = tc[t];
+        }
+}
+
 __global__ void alive_tri_count_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
                                        const uint8_t* alive, int32_t* deg, uint8_t* tdead) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -508,17 +527,55 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_LAUNCH(alive_init_kernel, grid_for(nact, blk), blk, 0, s, init_alive, nact, alive.get(), core_int, nalive.get());
     DevBuf<uint8_t> tdead;
     LDS_CUDA(cudaMemsetAsync(deg.get(), 0, nact * sizeof(int32_t), s));
+    // the triangle list the peeling walks: all of T, or, when few vertices are alive,
+    // only the triangles whose three members are alive (the others never count)
+    DevBuf<int32_t> cta, ctb, ctc, cvi;
+    DevBuf<int64_t> cvp;
+    const int64_t* tvp = nullptr;
+    const int32_t *tvi = nullptr, *tta = nullptr, *ttb = nullptr, *ttc = nullptr;
+    int64_t tnt = 0;
     if (!tri) {
         LDS_LAUNCH(alive_degree_kernel, grid_for(nact, blk), blk, 0, s, g->rowptr.get(), g->col.get(), alive.get(), nact,
                    deg.get());
     } else {
-        ensure_vertex_triangles(g);
-        const int64_t ntri = g->ntri;
-        tdead.alloc(((ntri + 3) & ~3ll) + 4, s);
-        LDS_CUDA(cudaMemsetAsync(tdead.get(), 0, ((ntri + 3) & ~3ll) + 4, s));
-        if (ntri)
-            LDS_LAUNCH(alive_tri_count_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
-                       alive.get(), deg.get(), tdead.get());
+        ensure_triangles(g);
+        int32_t nal = 0;
+        LDS_CUDA(cudaMemcpyAsync(&nal, nalive.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        if (init_alive && (int64_t)nal * 4 < (int64_t)nact && g->ntri) {
+            const int64_t ntri = g->ntri;
+            DevBuf<int32_t> flag(ntri + 1, s);
+            DevBuf<int64_t> tpos(ntri + 1, s);
+            LDS_CUDA(cudaMemsetAsync(flag.get() + ntri, 0, sizeof(int32_t), s));
+            LDS_LAUNCH(tri_all_alive_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
+                       alive.get(), flag.get());
+            tnt = exclusive_scan_i32_to_i64(flag.get(), tpos.get(), ntri + 1, s);
+            cta.alloc(std::max<int64_t>(tnt, 1), s);
+            ctb.alloc(std::max<int64_t>(tnt, 1), s);
+            ctc.alloc(std::max<int64_t>(tnt, 1), s);
+            if (tnt)
+                LDS_LAUNCH(tri_compact_kernel, grid_for(ntri, blk), blk, 0, s, g->ta.get(), g->tb.get(), g->tc.get(), ntri,
+                           flag.get(), tpos.get(), cta.get(), ctb.get(), ctc.get());
+            build_vertex_triangles(cta.get(), ctb.get(), ctc.get(), tnt, nact, cvp, cvi, s);
+            tvp = cvp.get();
+            tvi = cvi.get();
+            tta = cta.get();
+            ttb = ctb.get();
+            ttc = ctc.get();
+        } else {
+            ensure_vertex_triangles(g);
+            tnt = g->ntri;
+            tvp = g->vt_ptr.get();
+            tvi = g->vt_idx.get();
+            tta = g->ta.get();
+            ttb = g->tb.get();
+            ttc = g->tc.get();
+        }
+        tdead.alloc(((tnt + 3) & ~3ll) + 4, s);
+        LDS_CUDA(cudaMemsetAsync(tdead.get(), 0, ((tnt + 3) & ~3ll) + 4, s));
+        if (tnt)
+            LDS_LAUNCH(alive_tri_count_kernel, grid_for(tnt, blk), blk, 0, s, tta, ttb, ttc, tnt, alive.get(), deg.get(),
+                       tdead.get());
     }
     int32_t remaining = 0;
     LDS_CUDA(cudaMemcpyAsync(&remaining, nalive.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -530,7 +587,7 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_CUDA(cudaMemcpyAsync(ctrl.get(), hctrl, sizeof(hctrl), cudaMemcpyHostToDevice, s));
     DevBuf<int32_t> F1(nact, s), A0(nact, s), A1(nact, s);
     // chunk queue: at most one chunk per vertex plus one per PEEL_CHUNK incidences
-    const int64_t incid = tri ? 3 * g->ntri : 2 * g->m;
+    const int64_t incid = tri ? 3 * tnt : 2 * g->m;
     const int64_t qcap = (int64_t)nact + incid / PEEL_CHUNK + 1;
     DevBuf<int32_t> qv(qcap, s);
     DevBuf<int64_t> qs(qcap, s);
@@ -546,11 +603,11 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     bool trib = tri;
     const int64_t* rp = g->rowptr.get();
     const int32_t* cl = g->col.get();
-    const int64_t* vp = tri ? g->vt_ptr.get() : nullptr;
-    const int32_t* vi = tri ? g->vt_idx.get() : nullptr;
-    const int32_t* pa = tri ? g->ta.get() : nullptr;
-    const int32_t* pb = tri ? g->tb.get() : nullptr;
-    const int32_t* pc = tri ? g->tc.get() : nullptr;
+    const int64_t* vp = tri ? tvp : nullptr;
+    const int32_t* vi = tri ? tvi : nullptr;
+    const int32_t* pa = tri ? tta : nullptr;
+    const int32_t* pb = tri ? ttb : nullptr;
+    const int32_t* pc = tri ? ttc : nullptr;
     uint8_t* td = tri ? tdead.get() : nullptr;
     uint8_t* al = alive.get();
     int32_t* dg = deg.get();
