@@ -222,6 +222,12 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
 // 16-bit counters packed two per word.  Ties (equal words) are rare and are
 // broken by the internal ids, looked up only then.
 constexpr int HOT32 = 32768;
+// cooperative FW: hot vertices' global counts packed two per word (one atomic per
+// word in the flush), and the grid sized to the work (chunks per block; 0: one
+// block per SM whatever the size).  Both measured slower on the 1M-vertex graph
+// and its refinement subgraphs, so both are off.
+constexpr bool kPackedHot = false;
+constexpr int kCoopChunksPerBlock = 0;
 constexpr size_t OP32_SMEM = (size_t)HOT32 * 4 + (size_t)HOT32 * 2;
 
 // One pass over every stored slot.  ROWS: the row endpoints' counts are left
@@ -233,7 +239,8 @@ template <int U, class Word, bool ROWS, bool COOP>
 __device__ __forceinline__ void opass32_body(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
                                              const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks,
                                              const Word* word, const int32_t* __restrict__ perm, int32_t nhot,
-                                             int32_t* cnt, uint32_t* plane, Word* hword, uint32_t* hcnt2) {
+                                             int32_t* cnt, uint32_t* plane, Word* hword, uint32_t* hcnt2,
+                                             uint32_t* hglob = nullptr) {
     {
         const uint4* w4 = reinterpret_cast<const uint4*>(word);
         uint4* h4 = reinterpret_cast<uint4*>(hword);
@@ -321,11 +328,17 @@ __device__ __forceinline__ void opass32_body(const int32_t* __restrict__ col, co
         }
     }
     __syncthreads();
+    // hglob: the hot vertices' global counts, packed like the shared ones (a vertex
+    // receives at most its degree < 2^16 per iteration, so halves never carry)
     for (int i = threadIdx.x; i < (nhot + 1) >> 1; i += blockDim.x) {
         uint32_t v = hcnt2[i];
         if (v) {
-            if (v & 0xffffu) atomicAdd(cnt + 2 * i, (int)(v & 0xffffu));
-            if (v >> 16) atomicAdd(cnt + 2 * i + 1, (int)(v >> 16));
+            if (hglob) {
+                atomicAdd(hglob + i, v);
+            } else {
+                if (v & 0xffffu) atomicAdd(cnt + 2 * i, (int)(v & 0xffffu));
+                if (v >> 16) atomicAdd(cnt + 2 * i + 1, (int)(v >> 16));
+            }
         }
     }
 }
@@ -418,7 +431,7 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
     fw_coop32_kernel(const int32_t* __restrict__ col, const int32_t* __restrict__ chunk_nz0,
                      const int32_t* __restrict__ nzrow, int64_t nslots, int64_t nchunks, Word* word,
                      const int32_t* __restrict__ perm, int32_t nhot, int32_t* cnt, const int32_t* __restrict__ rowptr,
-                     uint32_t* planes, int32_t nact, int32_t i_first, int32_t K) {
+                     uint32_t* planes, int32_t nact, int32_t i_first, int32_t K, uint32_t* hglob) {
     cooperative_groups::grid_group grid = cooperative_groups::this_grid();
     extern __shared__ __align__(16) unsigned char smem[];
     Word* hword = reinterpret_cast<Word*>(smem);
@@ -429,29 +442,48 @@ __global__ void __launch_bounds__(OP_THREADS, 1)
         const int32_t i = i_first + it;
         uint32_t* plane = planes + (int64_t)it * nchunks;
         opass32_body<OP_UNROLL, Word, true, true>(col, chunk_nz0, nzrow, nslots, nchunks, word, perm, nhot, cnt, plane,
-                                                  hword, hcnt2);
+                                                  hword, hcnt2, kPackedHot ? hglob : nullptr);
         grid.sync();
-        for (int64_t p = tid; p < nact; p += nthreads) {
-            const int32_t t = __ldcg(cnt + p);
-            int32_t c = t;
-            const int32_t a = rowptr[p], b = rowptr[p + 1];
-            if (a < b) {
-                const int32_t wa = a >> 5, wb = (b - 1) >> 5;
-                for (int32_t q = wa; q <= wb; ++q) {
-                    uint32_t bits = __ldcg(plane + q);
-                    if (q == wa) bits &= FULL << (a & 31);
-                    if (q == wb) bits &= lanes_le((b - 1) & 31);
-                    c += __popc(bits);
+        // update: one work item per packed word of hot counts (two vertices), then one
+        // per cold vertex; without packing, one item per vertex
+        const int32_t hw = kPackedHot ? (nhot + 1) >> 1 : 0;
+        const int64_t items = (int64_t)hw + (nact - (kPackedHot ? nhot : 0));
+        for (int64_t it = tid; it < items; it += nthreads) {
+            int32_t p0, np;
+            uint32_t packed = 0;
+            int32_t tc = 0;
+            if (it < hw) {
+                p0 = (int32_t)(2 * it);
+                np = min(2, nhot - p0);
+                packed = __ldcg(hglob + it);
+                if (packed) hglob[it] = 0;
+            } else {
+                p0 = (kPackedHot ? nhot : 0) + (int32_t)(it - hw);
+                np = 1;
+                tc = __ldcg(cnt + p0);
+                if (tc) cnt[p0] = 0;
+            }
+            for (int32_t j = 0; j < np; ++j) {
+                const int32_t p = p0 + j;
+                int32_t c = it < hw ? (int32_t)((packed >> (16 * j)) & 0xffffu) : tc;
+                const int32_t a = rowptr[p], b = rowptr[p + 1];
+                if (a < b) {
+                    const int32_t wa = a >> 5, wb = (b - 1) >> 5;
+                    for (int32_t q = wa; q <= wb; ++q) {
+                        uint32_t bits = __ldcg(plane + q);
+                        if (q == wa) bits &= FULL << (a & 31);
+                        if (q == wb) bits &= lanes_le((b - 1) & 31);
+                        c += __popc(bits);
+                    }
+                }
+                if constexpr (std::is_same<Word, float>::value) {
+                    const float gam = __fdiv_rn(2.0f, (float)(i + 2));
+                    const float om = __fsub_rn(1.0f, gam);
+                    word[p] = __fadd_rn(__fmul_rn(om, word[p]), __fmul_rn(gam, (float)c));
+                } else {
+                    if (c) word[p] += (uint32_t)(2 * (i + 1)) * (uint32_t)c;
                 }
             }
-            if constexpr (std::is_same<Word, float>::value) {
-                const float gam = __fdiv_rn(2.0f, (float)(i + 2));
-                const float om = __fsub_rn(1.0f, gam);
-                word[p] = __fadd_rn(__fmul_rn(om, word[p]), __fmul_rn(gam, (float)c));
-            } else {
-                if (c) word[p] += (uint32_t)(2 * (i + 1)) * (uint32_t)c;
-            }
-            if (t) cnt[p] = 0;
         }
         grid.sync();
     }
@@ -760,6 +792,13 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
                                                                     OP32_SMEM));
         LDS_REQUIRE(per_sm >= 1, LDS_ECUDA, "fw: the cooperative pass cannot be resident");
         g->pass_kernel = "fw_coop32_kernel";
+        const unsigned cgrid =
+            kCoopChunksPerBlock > 0
+                ? (unsigned)std::max<int64_t>(
+                      1, std::min<int64_t>(grid, (nchunks + kCoopChunksPerBlock - 1) / kCoopChunksPerBlock))
+                : grid;
+        DevBuf<uint32_t> hglob(((nhot + 1) >> 1) + 1, s);
+        LDS_CUDA(cudaMemsetAsync(hglob.get(), 0, (((nhot + 1) >> 1) + 1) * sizeof(uint32_t), s));
         int i = 1;
         while (i <= N) {
             int32_t kk = std::min(K - stored, N - i + 1);
@@ -773,14 +812,16 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
             int64_t nsl = m, nch = nchunks;
             int32_t nh = nhot, na = nact, i0 = i;
             void* wp = fp32 ? (void*)r32.get() : (void*)w32.get();
+            uint32_t* hg = hglob.get();
             void* args[] = {(void*)&pcol, (void*)&pz, (void*)&pnz, (void*)&nsl, (void*)&nch, (void*)&wp, (void*)&pperm,
-                            (void*)&nh, (void*)&pcnt, (void*)&prow, (void*)&pl, (void*)&na, (void*)&i0, (void*)&kk};
+                            (void*)&nh, (void*)&pcnt, (void*)&prow, (void*)&pl, (void*)&na, (void*)&i0, (void*)&kk,
+                            (void*)&hg};
             timer.start(s);
             if (fp32)
-                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<float>, dim3(grid), dim3(OP_THREADS), args,
-                                                     OP32_SMEM, s));
+                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<float>, dim3(cgrid), dim3(OP_THREADS),
+                                                     args, OP32_SMEM, s));
             else
-                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<uint32_t>, dim3(grid), dim3(OP_THREADS),
+                LDS_CUDA(cudaLaunchCooperativeKernel((void*)fw_coop32_kernel<uint32_t>, dim3(cgrid), dim3(OP_THREADS),
                                                      args, OP32_SMEM, s));
             g_launches.fetch_add(1, std::memory_order_relaxed);
             timer.stop(s, kk);
