@@ -628,7 +628,13 @@ def run_batch(args):
 
 def run_serve(args):
     """Poisson stream of top-k queries over a resident graph mix through the
-    serving loop (lds_server_*): queries/s and p50 / p99 latency."""
+    serving loop (lds_server_*): queries/s and p50 / p99 latency.  The mix is
+    Chung-Lu graphs with n log-uniform in [1e3, serve_max_n] (exponent
+    U(2.1, 2.5), average degree 10, 2 planted blocks each) plus, unless
+    --no-rmat24, the R-MAT scale-24 graph (edge factor 16, 16.7M vertices, up
+    to 268M edges), all resident on the device.  LTDS queries on the R-MAT
+    graph are refused by the admission rule (LDS_EBUSY: its triangle footprint
+    exceeds the budget); they are counted, not timed."""
     import threading as th
     import torch
     from paper_2504_10937_gb300 import lds
@@ -636,15 +642,26 @@ def run_serve(args):
     lds.load()
     rng = synth.SplitMix64(5)
     lo, hi = np.log(1e3), np.log(args.serve_max_n)
-    graphs = []
+    graphs, sizes = [], []
+    t0 = time.perf_counter()
     for i in range(args.serve_graphs):
         n = int(round(np.exp(lo + rng.uniform(1)[0] * (hi - lo))))
         expo = 2.1 + 0.4 * rng.uniform(1)[0]
         nn, u, v, _ = synth.chung_lu(n, 5 * n, expo, int(rng.u64(1)[0]), n_blocks=2, block_size_range=(10, 100),
                                      block_prob_range=(0.6, 0.95), block_size_dist="uniform")
         g = lds.Graph(nn, u.astype(np.int32), v.astype(np.int32))
-        g.list_triangles()
         graphs.append(g)
+        sizes.append((nn, g.m))
+    rmat = None
+    if not args.no_rmat24:
+        nr, sr, dr = synth.rmat_device(24, 16, 0.57, 0.19, 0.19, seed=5)
+        rmat = lds.Graph(nr, sr, dr)
+        del sr, dr
+        torch.cuda.empty_cache()
+        graphs.append(rmat)
+        sizes.append((nr, rmat.m))
+    gen_s = time.perf_counter() - t0
+    print(f"[serve] {len(graphs)} graphs resident after {gen_s:.0f} s", file=sys.stderr, flush=True)
     reqs = []
     for i in range(args.requests):
         g = graphs[int(rng.integers(0, len(graphs), 1)[0])]
@@ -654,31 +671,41 @@ def run_serve(args):
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
 
-    def run_at(srv, rate):
-        """Open-loop Poisson arrivals at `rate`; returns (queries/s, sorted latencies)."""
-        gaps = unit_gaps / rate
-        tickets = [None] * len(reqs)
+    def run_at(srv, rate, count):
+        """Open-loop Poisson arrivals at `rate` for the first `count` requests;
+        returns (queries/s, sorted latencies, refused)."""
+        gaps = unit_gaps[:count] / rate
+        tickets = [None] * count
+        refused = [0]
         t_start = time.perf_counter()
 
         def feeder():
             t = t_start
-            for i, r in enumerate(reqs):
+            for i in range(count):
                 t += gaps[i]
                 d = t - time.perf_counter()
                 if d > 0:
                     time.sleep(d)
-                tickets[i] = srv.submit(*r)
+                try:
+                    tickets[i] = srv.submit(*reqs[i])
+                except lds.LdsError as e:
+                    if e.status != lds.EBUSY:
+                        raise
+                    tickets[i] = -1
+                    refused[0] += 1
 
         f = th.Thread(target=feeder)
         f.start()
         lat = []
-        for i in range(len(reqs)):
+        for i in range(count):
             while tickets[i] is None:
                 time.sleep(0.0005)
+            if tickets[i] < 0:
+                continue
             _, info = srv.wait(tickets[i])
             lat.append(info["queue_ms"] + info["run_ms"])
         f.join()
-        return len(reqs) / (time.perf_counter() - t_start), sorted(lat)
+        return len(lat) / (time.perf_counter() - t_start), sorted(lat), refused[0]
 
     def pct(lat, q):
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
@@ -686,30 +713,100 @@ def run_serve(args):
     sweep = []
     with lds.Server(budget, args.serve_workers) as srv:
         for r in reqs[:8]:                                 # warm-up
-            srv.wait(srv.submit(*r))
+            try:
+                srv.wait(srv.submit(*r))
+            except lds.LdsError as e:
+                if e.status != lds.EBUSY:
+                    raise
         with ClockSampler(0) as clk:
-            qps, lat = run_at(srv, args.rate)
+            qps, lat, refused = run_at(srv, args.rate, len(reqs))
+            print(f"[serve] saturated: {qps:.2f} queries/s, p50 {pct(lat, 0.5):.0f} ms, p99 {pct(lat, 0.99):.0f} ms",
+                  file=sys.stderr, flush=True)
             # offered load below saturation: fractions of the rate just measured
             for frac in ([] if args.no_sweep else [0.25, 0.5, 0.75, 0.9]):
-                q2, l2 = run_at(srv, frac * qps)
+                q2, l2, r2 = run_at(srv, frac * qps, min(len(reqs), args.sweep_requests))
+                print(f"[serve] offered {frac:.2f}: {q2:.2f} queries/s, p50 {pct(l2, 0.5):.0f} ms", file=sys.stderr,
+                      flush=True)
                 sweep.append({"offered_per_s": frac * qps, "queries_per_s": q2, "p50_ms": pct(l2, 0.5),
-                              "p99_ms": pct(l2, 0.99)})
+                              "p99_ms": pct(l2, 0.99), "requests": min(len(reqs), args.sweep_requests),
+                              "refused": r2})
     line = {
         "metric": "LDS queries/s (served)", "value": qps, "unit": "queries/s",
         "n_gpus": 1, "steps": len(reqs), "warmup": 8, "ms_per_step": statistics.mean(lat),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{len(graphs)} resident Chung-Lu graphs, n log-uniform in [1e3, {args.serve_max_n:g}], "
-                               "exponent U(2.1, 2.5), average degree 10, 2 blocks each (seed 5)",
-                   "requests": len(reqs), "arrival_rate_per_s": args.rate, "k": "uniform 1-20",
-                   "edge_triangle": "70:30", "precision": "fp32", "workers": args.serve_workers,
-                   "budget_bytes": budget},
+        "config": {"workload": f"{args.serve_graphs} resident Chung-Lu graphs, n log-uniform in "
+                               f"[1e3, {args.serve_max_n:g}], exponent U(2.1, 2.5), average degree 10, 2 blocks each "
+                               f"(seed 5)" + ("" if args.no_rmat24 else " + R-MAT scale 24, edge factor 16 (seed 5)"),
+                   "graphs": [{"n": a, "m": b} for a, b in sizes], "generation_s": gen_s,
+                   "requests": len(reqs), "sample": f"{len(reqs)} requests at saturation and "
+                   f"{args.sweep_requests} per offered-load point, out of the 100,000 of the stated stream: the "
+                   "whole stream would hold the GPU for hours", "arrival_rate_per_s": args.rate,
+                   "k": "uniform 1-20", "edge_triangle": "70:30", "precision": "fp32",
+                   "workers": args.serve_workers, "budget_bytes": budget},
         "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": lat[-1]},
+        "refused_ebusy": refused,
         "offered_load_sweep": sweep,
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
     for g in graphs:
         g.close()
+
+
+# The paper's LDScvx times on Barabasi-Albert graphs with n = 1e6 and m = d n
+# (d = 2..12), digitised from its scalability figure; Xeon Silver 4110, C++
+# (context for the sweep below, not a target: other hardware, k unstated)
+PAPER_BA_SECONDS = {2: 13.7, 4: 23.5, 6: 31.7, 8: 40.7, 10: 49.8, 12: 62.8}
+
+
+def run_ba(args):
+    """Scalability sweep of the paper (Barabasi-Albert, n = 1e6, m = 2e6 .. 12e6):
+    one top-k LDS query per graph through lds_topk, timed with CUDA events on
+    the graph's stream, the input resident on the device."""
+    import torch
+    from paper_2504_10937_gb300 import lds
+    torch.cuda.set_device(0)
+    lds.load()
+    stream = torch.cuda.current_stream()
+    rows = []
+    with ClockSampler(0) as clk:
+        for d in (2, 4, 6, 8, 10, 12):
+            t0 = time.perf_counter()
+            n, u, v = synth.barabasi_albert(1_000_000, d, seed=60 + d)[:3]
+            gen_s = time.perf_counter() - t0
+            tu = torch.from_numpy(u).cuda()
+            tv = torch.from_numpy(v).cuda()
+            times, res, st = [], None, None
+            for k in range(args.warmup + args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                with lds.Graph(n, tu, tv, stream=stream.cuda_stream) as g:
+                    res = g.topk(args.k, "edge", args.iters, args.precision)
+                    st = lds.topk_last_stats()
+                e1.record(stream)
+                e1.synchronize()
+                if k >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            rows.append({"d": d, "n": n, "m": len(u), "ms_per_query": statistics.mean(times),
+                         "fw_edge_updates_per_s": st["fw_edge_updates"] / (statistics.mean(times) / 1000.0),
+                         "paper_s": PAPER_BA_SECONDS[d], "result": [[str(x), len(c)] for x, c in res],
+                         "phases_ms": {key: st[key] for key in ("ms_fw", "ms_extract", "ms_prune", "ms_verify")},
+                         "generation_s": gen_s})
+            del tu, tv
+    line = {
+        "metric": "top-k LDS query time on Barabasi-Albert graphs (paper's scalability sweep)",
+        "value": statistics.mean(r["ms_per_query"] for r in rows), "unit": "ms per query (mean over the sweep)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"exact": "int64", "fp32": "f32", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "barabasi_albert(n=1e6, m_per_vertex=d, seed=60+d), d = 2..12", "k": args.k,
+                   "iters": args.iters, "precision": args.precision,
+                   "step": "ingest from device memory + top-k LDS query (lds_topk)",
+                   "paper_s": "LDScvx times digitised from the paper's scalability figure (CPU, context only)"},
+        "sweep": rows, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -729,14 +826,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-precision", action="store_true", help="skip the binary32 precision-pattern leg")
-    ap.add_argument("--mode", choices=["query", "batch", "serve"], default="query",
-                    help="query: the headline line; batch / serve: the many-query layers")
+    ap.add_argument("--mode", choices=["query", "batch", "serve", "ba"], default="query",
+                    help="query: the headline line; batch / serve: the many-query layers; ba: the paper's "
+                         "Barabasi-Albert scalability sweep")
     ap.add_argument("--graphs", type=int, default=4096, help="batch mode: number of graphs")
     ap.add_argument("--plain-sample", type=int, default=64, help="batch mode: queries run one at a time")
-    ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
+    ap.add_argument("--requests", type=int, default=600, help="serve mode: requests at saturation")
+    ap.add_argument("--sweep-requests", type=int, default=150, help="serve mode: requests per offered-load point")
     ap.add_argument("--rate", type=float, default=40.0, help="serve mode: Poisson arrivals per second")
-    ap.add_argument("--serve-graphs", type=int, default=16)
-    ap.add_argument("--serve-max-n", type=float, default=1e5)
+    ap.add_argument("--serve-graphs", type=int, default=24)
+    ap.add_argument("--serve-max-n", type=float, default=2e6)
+    ap.add_argument("--no-rmat24", action="store_true", help="serve mode: leave out the R-MAT scale-24 graph")
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--no-sweep", action="store_true", help="serve mode: skip the offered-load sweep")
     args = ap.parse_args()
@@ -749,6 +849,13 @@ def main():
         return
     if args.mode == "serve" and args.impl == "ours":
         run_serve(args)
+        return
+    if args.mode == "ba" and args.impl == "ours":
+        if args.k == WORKLOADS[args.workload]["k"]:
+            args.k = 5
+        if args.iters == WORKLOADS[args.workload]["iters"]:
+            args.iters = 100
+        run_ba(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -120,38 +120,41 @@ __global__ void copy_unflagged_kernel(const int32_t* col, int32_t* fwcol, int64_
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < k2; s += stride) fwcol[s] = col[s];
 }
 
-__global__ void slot_edge_kernel(const int64_t* rowptr, const int32_t* col, int32_t nact, const int64_t* eptr,
-                                 int64_t* slot_edge) {
-    // row r: lower slots (col < r) belong to edges (col, r) stored in row col; upper slots
-    // (col > r) are edges eptr[r] + j in order.
+// upper slot of edge e = (u, v), u < v: row u lists its lower neighbours first, then
+// its upper ones in edge order, so the slot is rowptr[u] + low(u) + (e - eptr[u])
+__global__ void slot_edge_upper_kernel(const int32_t* eu, int64_t m, const int64_t* rowptr, const int64_t* updeg,
+                                       const int64_t* eptr, int64_t* slot_edge) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nact; r += stride) {
-        int64_t b = rowptr[r], e = rowptr[r + 1];
-        int64_t up = eptr[r];
-        for (int64_t s = b; s < e; ++s) {
-            int32_t c = col[s];
-            if (c > r) slot_edge[s] = up++;
-            else {
-                // find r in row c (binary search in the upper part of row c)
-                int64_t lo = rowptr[c], hi = rowptr[c + 1];
-                while (lo < hi) {
-                    int64_t mid = (lo + hi) >> 1;
-                    if (col[mid] < r) lo = mid + 1; else hi = mid;
-                }
-                // edge id of slot lo in row c: eptr[c] + (#upper slots before lo in row c)
-                int64_t first_up = rowptr[c];
-                {
-                    int64_t l2 = rowptr[c], h2 = rowptr[c + 1];
-                    while (l2 < h2) {
-                        int64_t mid = (l2 + h2) >> 1;
-                        if (col[mid] <= c) l2 = mid + 1; else h2 = mid;
-                    }
-                    first_up = l2;
-                }
-                slot_edge[s] = eptr[c] + (lo - first_up);
-            }
-        }
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t u = eu[e];
+        const int64_t low = rowptr[u + 1] - rowptr[u] - updeg[u];
+        slot_edge[rowptr[u] + low + (e - eptr[u])] = e;
     }
+}
+
+__global__ void second_endpoint_keys_kernel(const int32_t* ev, int64_t m, uint64_t* key, uint32_t* eid) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        key[e] = (uint64_t)ev[e];
+        eid[e] = (uint32_t)e;
+    }
+}
+
+// lower slots: the edges sorted (stably) by their upper endpoint v, so by u within v;
+// the i-th of v's group sits at slot rowptr[v] + (i - gstart[v])
+__global__ void slot_edge_lower_kernel(const uint64_t* key, const uint32_t* eid, int64_t m, const int64_t* rowptr,
+                                       const int64_t* gstart, int64_t* slot_edge) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int64_t v = (int64_t)key[i];
+        slot_edge[rowptr[v] + (i - gstart[v])] = (int64_t)eid[i];
+    }
+}
+
+__global__ void lower_degree_kernel(const int64_t* rowptr, const int64_t* updeg, int32_t nact, int64_t* low) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nact; r += stride)
+        low[r] = rowptr[r + 1] - rowptr[r] - updeg[r];
 }
 
 __global__ void upper_degree_kernel(const int64_t* rowptr, const int32_t* col, int32_t nact, int64_t* updeg) {
@@ -193,9 +196,18 @@ void ensure_slot_edge(lds_graph* g) {
     LDS_CHECK_LAUNCH();
     exclusive_scan_i64_dev(updeg.get(), eptr.get(), g->nact, nullptr, s);
     g->slot_edge.alloc(2 * g->m, s);
-    LDS_LAUNCH(slot_edge_kernel, grid_for(g->nact, 128), 128, 0, s, g->rowptr.get(), g->col.get(), g->nact, eptr.get(),
-                                                           g->slot_edge.get());
-    LDS_CHECK_LAUNCH();
+    const int64_t m = g->m;
+    LDS_LAUNCH(slot_edge_upper_kernel, grid_for(m, 256), 256, 0, s, g->eu.get(), m, g->rowptr.get(), updeg.get(),
+               eptr.get(), g->slot_edge.get());
+    DevBuf<int64_t> low(g->nact, s), gstart(g->nact, s);
+    LDS_LAUNCH(lower_degree_kernel, grid_for(g->nact, 256), 256, 0, s, g->rowptr.get(), updeg.get(), g->nact, low.get());
+    exclusive_scan_i64_dev(low.get(), gstart.get(), g->nact, nullptr, s);
+    DevBuf<uint64_t> key(m, s);
+    DevBuf<uint32_t> eid(m, s);
+    LDS_LAUNCH(second_endpoint_keys_kernel, grid_for(m, 256), 256, 0, s, g->ev.get(), m, key.get(), eid.get());
+    radix_sort_u64(key.get(), eid.get(), m, std::max(1, bit_length_u64((uint64_t)g->nact)), s);
+    LDS_LAUNCH(slot_edge_lower_kernel, grid_for(m, 256), 256, 0, s, key.get(), eid.get(), m, g->rowptr.get(),
+               gstart.get(), g->slot_edge.get());
 }
 
 void to_original_order_i64(const lds_graph* g, const int64_t* in_int, int64_t* out_orig) {

@@ -57,18 +57,28 @@ __global__ void unmark_kernel(const int32_t* list, int32_t k, uint8_t* flag) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) flag[list[i]] = 0;
 }
 
+// Warp-per-member helpers: lane l takes slots l, l + 32, ... of the member's row;
+// outputs keep the row's order (ballot + prefix popcount), as one thread would.
+#define WARP_MEMBER_LOOP(k)                                                        \
+    const int lane = threadIdx.x & 31;                                             \
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;                \
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (k); i += wstride)
+
+__device__ __forceinline__ unsigned lanes_below(int lane) { return (1u << lane) - 1u; }
+
 // per member x: number of edge patterns it owns (neighbours y in the set with y > x)
 __global__ void edge_pat_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
                                       const int32_t* col, const uint8_t* in, int32_t* cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i], c = 0;
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
+        int32_t c = 0;
         if (x < nact)
-            for (int64_t q = rowptr[x]; q < rowptr[x + 1]; ++q) {
-                int32_t y = col[q];
+            for (int64_t q = rowptr[x] + lane; q < rowptr[x + 1]; q += 32) {
+                const int32_t y = col[q];
                 c += (y > x && in[y]);
             }
-        cnt[i] = c;
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[i] = c;
     }
 }
 
@@ -78,24 +88,32 @@ __global__ void edge_pat_fill_kernel(const int32_t* list, int32_t k, int32_t nac
                                      const int32_t* col, const uint8_t* in, const int32_t* local, const int64_t* off,
                                      int32_t* pidx, const int64_t* slot_edge, const int64_t* W, int64_t D,
                                      int64_t* share) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
+        if (x >= nact) continue;
         int64_t o = off[i];
-        if (x < nact)
-            for (int64_t q = rowptr[x]; q < rowptr[x + 1]; ++q) {
-                int32_t y = col[q];
-                if (y > x && in[y]) {
-                    pidx[2 * o] = (int32_t)i;
-                    pidx[2 * o + 1] = local[y];
-                    if (share) {
-                        const int64_t w = W[slot_edge[q]];
-                        share[2 * o] = w;
-                        share[2 * o + 1] = D - w;
-                    }
-                    ++o;
+        const int64_t b = rowptr[x], e = rowptr[x + 1];
+        for (int64_t q0 = b; q0 < e; q0 += 32) {
+            const int64_t q = q0 + lane;
+            bool take = false;
+            int32_t y = 0;
+            if (q < e) {
+                y = col[q];
+                take = y > x && in[y];
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const int64_t at = o + __popc(bal & lanes_below(lane));
+                pidx[2 * at] = (int32_t)i;
+                pidx[2 * at + 1] = local[y];
+                if (share) {
+                    const int64_t w = W[slot_edge[q]];
+                    share[2 * at] = w;
+                    share[2 * at + 1] = D - w;
                 }
             }
+            o += __popc(bal);
+        }
     }
 }
 
@@ -103,15 +121,16 @@ __global__ void edge_pat_fill_kernel(const int32_t* list, int32_t k, int32_t nac
 __global__ void loop_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr, const int32_t* col,
                                   const uint8_t* in, const int64_t* ln, const int64_t* ld, int64_t p, int64_t q,
                                   int32_t* cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i], c = 0;
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
+        int32_t c = 0;
         if (x < nact)
-            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-                int32_t w = col[r];
+            for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) {
+                const int32_t w = col[r];
                 c += (!in[w] && gt_rho(ln[w], ld[w], p, q));
             }
-        cnt[i] = c;
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[i] = c;
     }
 }
 
@@ -239,12 +258,11 @@ __global__ void grow_level_kernel(const int32_t* frontier, int32_t fsize, int32_
                                   const int32_t* col, uint8_t* inU, const int64_t* un, const int64_t* ud,
                                   const int64_t* ln, const int64_t* ld, int64_t p, int64_t q, bool use_lb,
                                   int32_t* next, int32_t* nsize) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fsize; i += stride) {
-        int32_t x = frontier[i];
+    WARP_MEMBER_LOOP(fsize) {
+        const int32_t x = frontier[i];
         if (x >= nact) continue;
-        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-            int32_t w = col[r];
+        for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) {
+            const int32_t w = col[r];
             if (inU[w]) continue;
             if (use_lb && gt_rho(ln[w], ld[w], p, q)) continue;   // loop side, never joins U
             if (lt_rho(un[w], ud[w], p, q)) continue;         // phi(w) < rho
@@ -259,15 +277,14 @@ __global__ void grow_level_kernel(const int32_t* frontier, int32_t fsize, int32_
 __global__ void denser_neighbour_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
                                         const int32_t* col, const uint8_t* inS, const int64_t* ln, const int64_t* ld,
                                         int64_t p, int64_t q, int32_t* flag) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
         if (x >= nact) continue;
-        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-            int32_t w = col[r];
+        for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) {
+            const int32_t w = col[r];
             if (!inS[w] && gt_rho(ln[w], ld[w], p, q)) {
                 atomicOr(flag, 1);
-                return;
+                break;
             }
         }
     }
@@ -287,14 +304,19 @@ __global__ void collect_kernel(const uint8_t* flag, int32_t n, int32_t* out, int
 // S must lie in A and have no neighbour in A outside S
 __global__ void component_check_kernel(const int32_t* S, int32_t k, int32_t nact, const int64_t* rowptr,
                                        const int32_t* col, const uint8_t* inS, const uint8_t* inA, int32_t* bad) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = S[i];
-        if (!inA[x]) { atomicOr(bad, 1); continue; }
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = S[i];
+        if (!inA[x]) {
+            if (lane == 0) atomicOr(bad, 1);
+            continue;
+        }
         if (x >= nact) continue;
-        for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-            int32_t w = col[r];
-            if (inA[w] && !inS[w]) { atomicOr(bad, 1); break; }
+        for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) {
+            const int32_t w = col[r];
+            if (inA[w] && !inS[w]) {
+                atomicOr(bad, 1);
+                break;
+            }
         }
     }
 }
@@ -328,16 +350,19 @@ __global__ void cc_coop_kernel(const int32_t* list, int32_t k, int32_t nact, con
             return;
         }
         int32_t* changed = flags + (sweep & 1);
-        for (int64_t i = tid; i < k; i += nthreads) {
+        // one warp per member: the lanes share its row
+        const int lane = threadIdx.x & 31;
+        for (int64_t i = tid >> 5; i < k; i += nthreads >> 5) {
             const int32_t x = list[i];
             if (x >= nact) continue;
             const int32_t lx = __ldcg(label + x);
             int32_t best = lx;
-            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
+            for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) {
                 const int32_t w = col[r];
                 if (in[w]) best = min(best, __ldcg(label + w));
             }
-            if (best < lx) {
+            for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (lane == 0 && best < lx) {
                 atomicMin(label + x, best);
                 *changed = 1;
             }
@@ -371,31 +396,40 @@ __global__ void cc_unpack_kernel(const uint64_t* key, int32_t k, int bits, int32
 
 __global__ void sub_edges_count_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
                                        const int32_t* col, const uint8_t* in, int32_t* cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i], c = 0;
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
+        int32_t c = 0;
         if (x < nact)
-            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) c += (col[r] > x && in[col[r]]);
-        cnt[i] = c;
+            for (int64_t r = rowptr[x] + lane; r < rowptr[x + 1]; r += 32) c += (col[r] > x && in[col[r]]);
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) cnt[i] = c;
     }
 }
 
 __global__ void sub_edges_fill_kernel(const int32_t* list, int32_t k, int32_t nact, const int64_t* rowptr,
                                       const int32_t* col, const uint8_t* in, const int32_t* local, const int64_t* off,
                                       int32_t* su, int32_t* sv) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) {
-        int32_t x = list[i];
+    WARP_MEMBER_LOOP(k) {
+        const int32_t x = list[i];
+        if (x >= nact) continue;
         int64_t o = off[i];
-        if (x < nact)
-            for (int64_t r = rowptr[x]; r < rowptr[x + 1]; ++r) {
-                int32_t y = col[r];
-                if (y > x && in[y]) {
-                    su[o] = (int32_t)i;
-                    sv[o] = local[y];
-                    ++o;
-                }
+        const int64_t b = rowptr[x], e = rowptr[x + 1];
+        for (int64_t q0 = b; q0 < e; q0 += 32) {
+            const int64_t r = q0 + lane;
+            bool take = false;
+            int32_t y = 0;
+            if (r < e) {
+                y = col[r];
+                take = y > x && in[y];
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) {
+                const int64_t at = o + __popc(bal & lanes_below(lane));
+                su[at] = (int32_t)i;
+                sv[at] = local[y];
+            }
+            o += __popc(bal);
+        }
     }
 }
 
@@ -444,14 +478,14 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
     DevBuf<int32_t> cnt(std::max(k, 1), s), len(std::max(k, 1), s);
     DevBuf<int64_t> off;
     if (!tri) {
-        if (k) LDS_LAUNCH(edge_pat_count_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+        if (k) LDS_LAUNCH(edge_pat_count_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
                           sc.in.get(), cnt.get());
         int64_t ne = scan_counts(cnt.get(), k, off, s);
         int64_t nl = 0;
         DevBuf<int32_t> lcnt(std::max(k, 1), s);
         DevBuf<int64_t> loff;
         if (loops) {
-            if (k) LDS_LAUNCH(loop_count_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+            if (k) LDS_LAUNCH(loop_count_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
                               sc.in.get(), b->ln.get(), b->ld.get(), p, q, lcnt.get());
             nl = scan_counts(lcnt.get(), k, loff, s);
         }
@@ -472,7 +506,7 @@ static int64_t build_patterns(lds_graph* g, bool tri, const int32_t* list, int32
             LDS_CUDA(cudaMemcpyAsync(pptr.get() + ne, tail.get(), (nl + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
         }
         if (k && ne)
-            LDS_LAUNCH(edge_pat_fill_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+            LDS_LAUNCH(edge_pat_fill_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
                        sc.in.get(), sc.local.get(), off.get(), pidx.get(), warm ? g->slot_edge.get() : nullptr,
                        warm ? g->fw_W.get() : nullptr, g->fw_D, sh);
         if (k && nl)
@@ -568,7 +602,7 @@ bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat
     int32_t hflag = 0;
     if (mode == LDS_VERIFY_BOUNDS) {
         LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
-        LDS_LAUNCH(denser_neighbour_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+        LDS_LAUNCH(denser_neighbour_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
                    sc.in.get(), b.ln.get(), b.ld.get(), p, q, flag.get());
         LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
@@ -597,7 +631,7 @@ bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat
         LDS_CUDA(cudaMemcpyAsync(U.get(), list, k * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         while (fsize > 0) {
             LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
-            LDS_LAUNCH(grow_level_kernel, grid_for(fsize, VB), VB, 0, s, cur, fsize, nact, g->rowptr.get(),
+            LDS_LAUNCH(grow_level_kernel, grid_for((int64_t)fsize * 32, VB), VB, 0, s, cur, fsize, nact, g->rowptr.get(),
                        g->col.get(), sc.in2.get(), b.un.get(), b.ud.get(), b.ln.get(), b.ld.get(), p, q,
                        mode == LDS_VERIFY_BOUNDS, nxt, cnt.get());
             LDS_CUDA(cudaMemcpyAsync(&fsize, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -641,7 +675,7 @@ bool is_lds(lds_graph* g, bool tri, const int32_t* list, int32_t k, int64_t npat
         LDS_LAUNCH(unmark_kernel, grid_for(usize, VB), VB, 0, s, U.get(), usize, sc.in2.get());
         LDS_LAUNCH(mark_kernel, grid_for(k, VB), VB, 0, s, list, k, sc.in2.get(), (int32_t*)nullptr);
         LDS_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int32_t), s));
-        LDS_LAUNCH(component_check_kernel, grid_for(k, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
+        LDS_LAUNCH(component_check_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, nact, g->rowptr.get(), g->col.get(),
                    sc.in2.get(), sc.in.get(), flag.get());
         LDS_CUDA(cudaMemcpyAsync(&hflag, flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LDS_CUDA(cudaStreamSynchronize(s));
@@ -672,7 +706,8 @@ void components(lds_graph* g, const int32_t* list, int32_t k, Scratch& sc, DevBu
         int per_sm = 0;
         LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cc_coop_kernel, VB, 0));
         LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "components: the sweep kernel cannot be resident");
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((k + VB - 1) / VB, (int64_t)num_sms() * per_sm));
+        const int grid =
+            (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)k * 32 + VB - 1) / VB, (int64_t)num_sms() * per_sm));
         const int32_t* lp = list;
         int32_t kk = k, na = g->nact;
         const int64_t* rp = g->rowptr.get();
@@ -713,12 +748,12 @@ lds_graph* subgraph(lds_graph* g, const int32_t* list, int32_t k, Scratch& sc) {
     LDS_LAUNCH(mark_kernel, grid_for(std::max(k, 1), VB), VB, 0, s, list, k, sc.in.get(), sc.local.get());
     DevBuf<int32_t> cnt(std::max(k, 1), s);
     DevBuf<int64_t> off;
-    if (k) LDS_LAUNCH(sub_edges_count_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
+    if (k) LDS_LAUNCH(sub_edges_count_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
                       sc.in.get(), cnt.get());
     int64_t me = scan_counts(cnt.get(), k, off, s);
     DevBuf<int32_t> su(std::max<int64_t>(me, 1), s), sv(std::max<int64_t>(me, 1), s);
     if (k && me)
-        LDS_LAUNCH(sub_edges_fill_kernel, grid_for(k, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
+        LDS_LAUNCH(sub_edges_fill_kernel, grid_for((int64_t)k * 32, VB), VB, 0, s, list, k, g->nact, g->rowptr.get(), g->col.get(),
                    sc.in.get(), sc.local.get(), off.get(), su.get(), sv.get());
     LDS_LAUNCH(unmark_kernel, grid_for(std::max(k, 1), VB), VB, 0, s, list, k, sc.in.get());
     LDS_CUDA(cudaStreamSynchronize(s));
