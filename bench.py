@@ -704,8 +704,18 @@ def run_serve(args):
                 continue
             _, info = srv.wait(tickets[i])
             lat.append(info["queue_ms"] + info["run_ms"])
+            runs.append((info["run_ms"], i))
         f.join()
         return len(lat) / (time.perf_counter() - t_start), sorted(lat), refused[0]
+
+    runs = []
+
+    def slowest(count=8):
+        out = []
+        for ms, i in sorted(runs, reverse=True)[:count]:
+            g, k, d, it, _ = reqs[i]
+            out.append({"run_ms": round(ms, 1), "n": g.n, "m": g.m, "density": d, "k": k})
+        return out
 
     def pct(lat, q):
         return lat[min(len(lat) - 1, int(q * (len(lat) - 1) + 0.5))]
@@ -720,8 +730,8 @@ def run_serve(args):
                     raise
         with ClockSampler(0) as clk:
             qps, lat, refused = run_at(srv, args.rate, len(reqs))
-            print(f"[serve] saturated: {qps:.2f} queries/s, p50 {pct(lat, 0.5):.0f} ms, p99 {pct(lat, 0.99):.0f} ms",
-                  file=sys.stderr, flush=True)
+            print(f"[serve] saturated: {qps:.2f} queries/s, p50 {pct(lat, 0.5):.0f} ms, p99 {pct(lat, 0.99):.0f} ms; "
+                  f"slowest {slowest(4)}", file=sys.stderr, flush=True)
             # offered load below saturation: fractions of the rate just measured
             for frac in ([] if args.no_sweep else [0.25, 0.5, 0.75, 0.9]):
                 q2, l2, r2 = run_at(srv, frac * qps, min(len(reqs), args.sweep_requests))
@@ -745,6 +755,7 @@ def run_serve(args):
                    "workers": args.serve_workers, "budget_bytes": budget},
         "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": lat[-1]},
         "refused_ebusy": refused,
+        "slowest_requests": slowest(),
         "offered_load_sweep": sweep,
         "clocks": clk.summary(),
     }

@@ -113,6 +113,19 @@ lds_status lds_get_triangles(lds_graph* g, int32_t* tri, lds_mem where);
  * LDS_TRIANGLE lists triangles first if needed. */
 lds_status lds_core_numbers(lds_graph* g, lds_density d, int64_t* core, lds_mem where);
 
+/* Compact numbers phi(u) (Def. 4; tr-compact for LDS_TRIANGLE, Def. 10) of every
+ * vertex, exactly, as reduced fractions num[u] / den[u] (int64[n] each; den >= 1,
+ * phi = 0 for a vertex in no edge / triangle).  By Thm. 1 and Thm. 4 they are the
+ * optimal loads r* of the convex program; here they come from the
+ * density-friendly decomposition (Sec. 4.2), one maximum flow of Alg. 8's
+ * network per split: at the mean ratio rho of a vertex set F (patterns inside the
+ * settled levels above plus F and touching F, over |F|), the largest minimum-cut
+ * source side is {u in F : phi(u) >= rho}, which is all of F exactly when F is
+ * one level.  Same answer as lds_topk's exact settle.  Errors: LDS_EINVAL,
+ * LDS_ENOMEM, LDS_ECUDA, LDS_EOVERFLOW (more than 2^31 - 1 patterns in one
+ * sub-problem). */
+lds_status lds_compact_numbers(lds_graph* g, lds_density d, int64_t* num, int64_t* den, lds_mem where);
+
 /* Results of lds_fw; every pointer may be NULL to skip that output.        */
 typedef struct {
     double*  r;        /* [n] loads r_u after `iters` iterations: EXACT gives R_u / D
@@ -369,7 +382,12 @@ lds_status lds_batch_autotune(int32_t count, const lds_query* queries, int32_t* 
 int32_t lds_debug_pick_next(int32_t nq, const int64_t* bytes, const uint8_t* graph_busy, int64_t free_bytes);
 
 /* Edge-density kernel choice for LDS_EXACT / LDS_FP32 (process-wide):
- *   0  automatic: the degree-oriented pass (each edge once, stored at its
+ *   0  automatic: a graph whose active vertices fit in shared memory (at
+ *      most 24,576, every scaled load below 2^32) and with few edges (at most
+ *      49,152) runs on one thread-block
+ *      cluster of 8 CTAs, each holding every load word and 1/8 of the edges,
+ *      the counts reduced and the new loads broadcast through distributed
+ *      shared memory; otherwise the degree-oriented pass (each edge once, stored at its
  *      lower-degree endpoint, hot loads in shared memory) with 32-bit load
  *      words when every scaled load fits 32 bits, else with 64-bit keys
  *      (load, id), else variant 1.  With 32-bit words the pass counts only
@@ -382,7 +400,10 @@ int32_t lds_debug_pick_next(int32_t nq, const int64_t* bytes, const uint8_t* gra
  *   3  as 0 with 32-bit words, both endpoints' receipts counted inside the
  *      pass, one pass launch and one update launch per iteration;
  *   4  as 0 with 32-bit words, one pass launch and one update launch per
- *      iteration.
+ *      iteration;
+ *   5  as 0 without the cluster form (the cooperative launch for every size);
+ *   6  as 0 with the cluster form for every graph that fits, whatever its
+ *      edge count.
  * All compute the same iterates.  Errors: LDS_EINVAL. */
 lds_status lds_set_fw_variant(int32_t variant);
 

@@ -865,7 +865,7 @@ void extract_sg(lds_graph* g, SgState& st) {
     // long before the last candidate.
     const size_t ncand = ca.size();
     std::vector<long long> mnS(ncand), mxS(ncand), mnX(ncand), mxZ(ncand);
-    size_t checked = 0, batch = 256;
+    size_t checked = 0, batch = 16;
     auto ensure_checked = [&](size_t k) {
         while (checked <= k) {
             const size_t hi = std::min(ncand, checked + batch);

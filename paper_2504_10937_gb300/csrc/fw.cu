@@ -662,8 +662,21 @@ void fw_run(lds_graph* g, lds_density d, int32_t iters, lds_precision p, bool wa
     if (d == LDS_EDGE) {
         EdgeFwOut fo;
         LDS_CUDA(cudaEventRecord(e0, s));
-        bool fast = g_fw_variant != 1 && run_edge_fw_oriented(g, iters, p, true, want_last, fo, timer);
-        if (fast) {
+        // graphs whose active vertices fit in shared memory run on one thread-block cluster
+        bool clus = false;
+        if ((g_fw_variant == 0 || g_fw_variant == 6) && (p == LDS_EXACT || p == LDS_FP32)) {
+            if (want_last) g->fw_last.alloc(std::max<int64_t>(g->m, 1), s);
+            timer.start(s);
+            clus = fw_cluster_run(g, iters, p, want_last ? g->fw_last.get() : nullptr, g_fw_variant == 6);
+            if (clus) timer.stop(s, iters);
+            else g->fw_last.release();
+        }
+        bool fast = !clus && g_fw_variant != 1 && run_edge_fw_oriented(g, iters, p, true, want_last, fo, timer);
+        if (clus) {
+            LDS_CUDA(cudaEventRecord(e1, s));
+            g->pass_kernel = "fw_cluster_kernel";
+            g->pass_bytes = 12 * g->m + 8 * (int64_t)nact;
+        } else if (fast) {
             LDS_CUDA(cudaEventRecord(e1, s));
             const std::string pk(g->pass_kernel);
             g->pass_bytes = 4 * g->m + 8 * ((g->m + 31) / 32) + 4 * g->fwv_nz +
@@ -841,7 +854,7 @@ void lds_set_pass_profiling(int32_t on) { g_pass_profiling = on != 0; }
 
 lds_status lds_set_fw_variant(int32_t variant) {
     return guard([&] {
-        LDS_REQUIRE(variant >= 0 && variant <= 4, LDS_EINVAL, "lds_set_fw_variant: variant must be 0 to 4");
+        LDS_REQUIRE(variant >= 0 && variant <= 6, LDS_EINVAL, "lds_set_fw_variant: variant must be 0 to 6");
         g_fw_variant = variant;
     });
 }

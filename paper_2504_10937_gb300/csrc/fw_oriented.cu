@@ -726,7 +726,7 @@ bool run_edge_fw_oriented(lds_graph* g, int N, lds_precision p, bool want_w, boo
     // in the vertex update but launches pass and update once per iteration; the
     // default runs many iterations per cooperative launch
     const bool rows = g_fw_variant != 3;
-    const bool coop = g_fw_variant == 0;
+    const bool coop = g_fw_variant == 0 || g_fw_variant == 5 || g_fw_variant == 6;
     bool use32 = g_fw_variant != 2 && maxdeg < 65536 && (p == LDS_FP32 || (unsigned __int128)maxdeg * (unsigned __int128)Dn < ((unsigned __int128)1 << 32));
     if (!use32) {
         if (p == LDS_EXACT) {

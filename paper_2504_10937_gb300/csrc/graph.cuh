@@ -107,6 +107,11 @@ void to_original_order_f64(const lds_graph* g, const double* in_int, double* out
 // Batched on-chip Frank-Wolfe (fw_batch.cu): tunes the threads per graph of every
 // size bucket among the given graphs (kept for the process), and reports the choice.
 void fw_batch_autotune(int32_t count, lds_graph** graphs, int32_t iters, lds_precision p);
+// lds_fw's edge-density iterations of one small graph on a thread-block cluster
+// (fw_batch.cu); false when the graph does not fit, or (unless `any_size`) has
+// more edges than the cluster form beats the grid-wide form on (the caller runs
+// another path).
+bool fw_cluster_run(lds_graph* g, int32_t N, lds_precision p, uint8_t* last, bool any_size);
 int32_t fw_batch_threads(int32_t nact);
 
 }  // namespace lds

@@ -11,7 +11,8 @@
 //     is self-densest is certified by IsLDS / IsLTDS on G (or dropped); one that
 //     is not is refined.  A refinement that returns the component unchanged is
 //     retried with 2N, 4N, 8N iterations and then settled exactly (compact
-//     numbers of G[C] by repeated flows, LDSs of G[C] by their level sets, each
+//     numbers of G[C] by a divide and conquer of maximum flows over the
+//     density-friendly decomposition, LDSs of G[C] by their level sets, each
 //     certified on G).
 //   * Completeness: every group is processed, except that once k sets are
 //     certified a group whose vertices all have ub < rho_k is skipped.
@@ -23,6 +24,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <unordered_map>
 
 #include "extract_sg.cuh"
 #include "flow.cuh"
@@ -152,45 +154,150 @@ __global__ void unsort_keys_kernel(const uint64_t* key, int64_t k, int32_t* out)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = (int32_t)key[i];
 }
 
-// ---- exact settle helpers (compact numbers of a small vertex set)
+// ---- exact settle: compact numbers of G[C] by divide and conquer over the
+// density-friendly decomposition.  A sub-problem is a vertex set F with every
+// vertex of a higher level settled above it and every vertex of a lower level
+// below it; its patterns are those inside (above + F) with a member in F, each
+// reduced to its members in F.  Vertex states:
+constexpr uint8_t ES_BELOW = 0, ES_ABOVE = 1, ES_IN = 2;
+constexpr unsigned ES_FULL = 0xffffffffu;
 
-__global__ void reduce_patterns_count_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* inB,
-                                             int32_t* len) {
+// incidences: deg[v] = patterns with member v
+__global__ void es_inc_count_kernel(const int32_t* pidx, int64_t nnz, int32_t* deg) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < nnz; a += stride) atomicAdd(deg + pidx[a], 1);
+}
+
+__global__ void es_inc_fill_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const int64_t* vptr,
+                                   int32_t* cursor, int32_t* vinc) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride)
+        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a) {
+            const int32_t v = pidx[a];
+            vinc[vptr[v] + atomicAdd(cursor + v, 1)] = (int32_t)j;
+        }
+}
+
+// members of F enter the sub-problem (state, local index) or leave it
+__global__ void es_enter_kernel(const int32_t* F, int32_t nf, uint8_t* st, int32_t* freeidx) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) {
+        st[F[i]] = ES_IN;
+        freeidx[F[i]] = (int32_t)i;
+    }
+}
+
+__global__ void es_leave_kernel(const int32_t* F, int32_t nf, uint8_t* st, uint8_t to, int64_t p, int64_t q,
+                                int64_t* phin, int64_t* phid) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) {
+        st[F[i]] = to;
+        if (to == ES_ABOVE) {
+            phin[F[i]] = p;
+            phid[F[i]] = q;
+        }
+    }
+}
+
+// one warp per member v of F: the sub-problem's patterns through v that no member
+// below it touches and whose smallest member in F is v (each pattern once);
+// FILL writes their ids in incidence order
+template <bool FILL>
+__global__ void es_emit_kernel(const int32_t* F, int32_t nf, const int64_t* vptr, const int32_t* vinc,
+                               const int64_t* pptr, const int32_t* pidx, const uint8_t* st, int32_t* cnt,
+                               const int64_t* off, int32_t* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nf; i += nwarps) {
+        const int32_t v = F[i];
+        const int64_t a1 = vptr[v + 1];
+        int64_t o = FILL ? off[i] : 0;
+        for (int64_t base = vptr[v]; base < a1; base += 32) {
+            const int64_t a = base + lane;
+            bool keep = false;
+            int32_t j = 0;
+            if (a < a1) {
+                j = vinc[a];
+                keep = true;
+                for (int64_t b = pptr[j]; b < pptr[j + 1]; ++b) {
+                    const int32_t w = pidx[b];
+                    const uint8_t sw = st[w];
+                    if (sw == ES_BELOW || (sw == ES_IN && w < v)) {
+                        keep = false;
+                        break;
+                    }
+                }
+            }
+            const unsigned bal = __ballot_sync(ES_FULL, keep);
+            if (FILL && keep) out[o + __popc(bal & ((1u << lane) - 1u))] = j;
+            o += __popc(bal);
+        }
+        if (!FILL && lane == 0) cnt[i] = (int32_t)o;
+    }
+}
+
+// reduced patterns: their members in F as local indices
+__global__ void es_len_kernel(const int32_t* pats, int64_t nr, const int64_t* pptr, const int32_t* pidx,
+                              const uint8_t* st, int32_t* len) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += stride) {
+        const int32_t j = pats[r];
         int32_t c = 0;
-        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a) c += !inB[pidx[a]];
-        len[j] = c;
+        for (int64_t b = pptr[j]; b < pptr[j + 1]; ++b) c += st[pidx[b]] == ES_IN;
+        len[r] = c;
     }
 }
 
-__global__ void reduce_patterns_fill_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* inB,
-                                            const int32_t* freeidx, const int64_t* nptr, int32_t* nidx) {
+__global__ void es_fill_kernel(const int32_t* pats, int64_t nr, const int64_t* pptr, const int32_t* pidx,
+                               const uint8_t* st, const int32_t* freeidx, const int64_t* dptr, int32_t* ridx) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
-        int64_t o = nptr[j];
-        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a)
-            if (!inB[pidx[a]]) nidx[o++] = freeidx[pidx[a]];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += stride) {
+        const int32_t j = pats[r];
+        int64_t o = dptr[r];
+        for (int64_t b = pptr[j]; b < pptr[j + 1]; ++b)
+            if (st[pidx[b]] == ES_IN) ridx[o++] = freeidx[pidx[b]];
     }
 }
 
-__global__ void pattern_inside_kernel(const int64_t* pptr, const int32_t* pidx, int64_t np, const uint8_t* in,
-                                      int32_t* cnt) {
+__global__ void es_iota_kernel(int32_t* out, int32_t n) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int32_t c = 0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < np; j += stride) {
-        bool all = pptr[j + 1] > pptr[j];
-        for (int64_t a = pptr[j]; a < pptr[j + 1]; ++a) all &= in[pidx[a]] != 0;
-        c += all;
-    }
-    if (c) atomicAdd(cnt, c);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (int32_t)i;
 }
 
-__global__ void u8_count_kernel(const uint8_t* f, int64_t k, int32_t* cnt) {
+__global__ void u8_to_i32_kernel(const uint8_t* in, int64_t k, int32_t* out) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int32_t c = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) c += f[i] != 0;
-    if (c) atomicAdd(cnt, c);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += stride) out[i] = in[i] != 0;
+}
+
+// F split by the cut side: side 1 to X (in order), side 0 to Y (in order)
+__global__ void es_split_kernel(const int32_t* F, int32_t nf, const int32_t* side, const int64_t* pos, int32_t* X,
+                                int32_t* Y) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) {
+        if (side[i]) X[pos[i]] = F[i];
+        else Y[i - pos[i]] = F[i];
+    }
+}
+
+// one warp per vertex x (local id): 1 if a neighbour of x in G[C] has a higher
+// compact number (no LDS of G[C] contains x then)
+__global__ void es_higher_kernel(const int32_t* all, int32_t n, int32_t nact, const int64_t* rowptr, const int32_t* col,
+                                 const int32_t* to_local, const int64_t* phin, const int64_t* phid, uint8_t* flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+        const int32_t xi = all[x];
+        bool hi = false;
+        if (xi < nact) {
+            const i128 a = phin[x], b = phid[x];
+            for (int64_t e = rowptr[xi] + lane; e < rowptr[xi + 1] && !hi; e += 32) {
+                const int32_t y = to_local[col[e]];
+                hi = (i128)phin[y] * b > a * (i128)phid[y];
+            }
+        }
+        hi = __any_sync(ES_FULL, hi);
+        if (lane == 0) flag[x] = hi;
+    }
 }
 
 }  // namespace
@@ -330,16 +437,19 @@ struct Driver {
     void run();
 };
 
-void Driver::exact_settle(const int32_t* comp, int32_t csize) {
-    ++stats.exact_settled;
-    cudaStream_t s = st();
-    lds_graph* h = subgraph(G, comp, csize, sc);
-    struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+// Compact numbers of every vertex of h (Thm. 1 / Thm. 4: the optimal loads r*),
+// exactly, as reduced fractions phin / phid indexed by h's original ids, through
+// the density-friendly decomposition.  `all` receives h's internal id of every
+// original id.  Returns the number of maximum flows run.
+int64_t exact_compact_numbers(lds_graph* h, bool tri, DevBuf<int32_t>& all, DevBuf<int64_t>& phin,
+                              DevBuf<int64_t>& phid) {
+    cudaStream_t s = h->stream;
     if (tri) ensure_triangles(h);
     const int32_t n = h->n;
-    // patterns of G[comp] in h's original ids (= positions in comp)
+    int64_t flows = 0;
+    // patterns of G[comp] over local ids (h's original ids = positions in comp)
     Scratch shc(h);
-    DevBuf<int32_t> all(std::max(n, 1), s);
+    all.alloc(std::max(n, 1), s);
     {
         std::vector<int32_t> ids(n);
         std::iota(ids.begin(), ids.end(), 0);
@@ -348,113 +458,161 @@ void Driver::exact_settle(const int32_t* comp, int32_t csize) {
         map_ids(orig.get(), h->to_int.get(), n, all.get(), s);   // internal ids of h, in original order
         LDS_CUDA(cudaStreamSynchronize(s));
     }
-    // patterns over h's internal ids with local index = original id
     DevBuf<int64_t> pptr;
     DevBuf<int32_t> pidx;
-    int64_t np = build_all_patterns(h, tri, all.get(), n, shc, pptr, pidx);
-    // decomposition: phi per local vertex as (num, den)
-    std::vector<int64_t> phin(n, -1), phid(n, 1);
-    std::vector<uint8_t> inB(n, 0);
-    DevBuf<uint8_t> dB(std::max(n, 1), s), side(std::max(n, 1), s);
-    DevBuf<int32_t> freeidx(std::max(n, 1), s), cnt(1, s);
-    int32_t assigned = 0;
-    while (assigned < n) {
-        // free vertices and their local indices
-        std::vector<int32_t> fidx(n, -1), freev;
-        for (int32_t x = 0; x < n; ++x)
-            if (!inB[x]) { fidx[x] = (int32_t)freev.size(); freev.push_back(x); }
-        const int32_t nf = (int32_t)freev.size();
-        copy_in(dB.get(), inB.data(), LDS_MEM_HOST, n, s);
-        copy_in(freeidx.get(), fidx.data(), LDS_MEM_HOST, n * sizeof(int32_t), s);
-        DevBuf<int32_t> len(std::max<int64_t>(np, 1) + 1, s);
-        LDS_CUDA(cudaMemsetAsync(len.get(), 0, (std::max<int64_t>(np, 1) + 1) * sizeof(int32_t), s));
-        if (np) LDS_LAUNCH(reduce_patterns_count_kernel, grid_for(np, DB), DB, 0, s, pptr.get(), pidx.get(), np, dB.get(),
-                           len.get());
-        DevBuf<int64_t> nptr(np + 1, s);
-        int64_t nidx = exclusive_scan_i32_to_i64(len.get(), nptr.get(), np + 1, s);
-        DevBuf<int32_t> ridx(std::max<int64_t>(nidx, 1), s);
-        if (np) LDS_LAUNCH(reduce_patterns_fill_kernel, grid_for(np, DB), DB, 0, s, pptr.get(), pidx.get(), np, dB.get(),
-                           freeidx.get(), nptr.get(), ridx.get());
-        // drop patterns that lie inside B (length 0): they cannot be cut and carry no free vertex;
-        // keep them out by counting only the non-empty ones
-        std::vector<int64_t> hptr(np + 1);
-        LDS_CUDA(cudaMemcpyAsync(hptr.data(), nptr.get(), (np + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        LDS_CUDA(cudaStreamSynchronize(s));
-        std::vector<int64_t> cptr(1, 0);
-        for (int64_t j = 0; j < np; ++j)
-            if (hptr[j + 1] > hptr[j]) cptr.push_back(hptr[j + 1]);
-        const int64_t nr = (int64_t)cptr.size() - 1;
-        DevBuf<int64_t> dptr(nr + 1, s);
-        copy_in(dptr.get(), cptr.data(), LDS_MEM_HOST, (nr + 1) * sizeof(int64_t), s);
-        // Dinkelbach from the ratio of taking every free vertex
-        int64_t p = nr, q = nf;
-        {
-            int64_t g = std::gcd(p, q);
-            if (g) { p /= g; q /= g; }
-        }
-        if (p == 0) q = 1;
-        std::vector<uint8_t> X(nf, 1);
-        for (int it = 0;; ++it) {
-            int64_t f = pattern_max_flow(dptr.get(), ridx.get(), (int32_t)nr, nf, p, q, nullptr, side.get(), false, s);
-            ++vst.flows;
-            int64_t value = q * nr - f;
-            std::vector<uint8_t> hs(nf);
-            LDS_CUDA(cudaMemcpyAsync(hs.data(), side.get(), nf, cudaMemcpyDeviceToHost, s));
-            LDS_CUDA(cudaStreamSynchronize(s));
-            if (value <= 0) {
-                X = hs;
-                break;
-            }
-            // ratio of the maximiser X
-            LDS_CUDA(cudaMemsetAsync(cnt.get(), 0, sizeof(int32_t), s));
-            LDS_LAUNCH(pattern_inside_kernel, grid_for(std::max<int64_t>(nr, 1), DB), DB, 0, s, dptr.get(), ridx.get(), nr,
-                       side.get(), cnt.get());
-            int32_t inside = 0;
-            LDS_CUDA(cudaMemcpyAsync(&inside, cnt.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            LDS_CUDA(cudaStreamSynchronize(s));
-            int64_t xs = 0;
-            for (uint8_t b : hs) xs += b;
-            int64_t g = std::gcd((int64_t)inside, xs);
-            p = inside / g;
-            q = xs / g;
-            LDS_REQUIRE(it < 4 * nf + 8, LDS_ETIMEOUT, "exact settle: Dinkelbach did not converge");
-        }
-        int64_t xs = 0;
-        for (uint8_t b : X) xs += b;
-        if (xs == 0) std::fill(X.begin(), X.end(), 1);      // ratio 0: everything left
-        for (int32_t i = 0; i < nf; ++i)
-            if (X[i]) {
-                int32_t x = freev[i];
-                phin[x] = p;
-                phid[x] = q;
-                inB[x] = 1;
-                ++assigned;
-            }
+    const int64_t np = build_all_patterns(h, tri, all.get(), n, shc, pptr, pidx);
+    int64_t nnz = 0;
+    if (np) LDS_CUDA(cudaMemcpyAsync(&nnz, pptr.get() + np, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaStreamSynchronize(s));
+    // vertex -> pattern incidences
+    DevBuf<int32_t> ideg(n + 1, s), cursor(std::max(n, 1), s), vinc(std::max<int64_t>(nnz, 1), s);
+    DevBuf<int64_t> vptr(n + 1, s);
+    LDS_CUDA(cudaMemsetAsync(ideg.get(), 0, (n + 1) * sizeof(int32_t), s));
+    LDS_CUDA(cudaMemsetAsync(cursor.get(), 0, std::max(n, 1) * sizeof(int32_t), s));
+    if (nnz) LDS_LAUNCH(es_inc_count_kernel, grid_for(nnz, DB), DB, 0, s, pidx.get(), nnz, ideg.get());
+    exclusive_scan_i32_to_i64(ideg.get(), vptr.get(), n + 1, s);
+    if (np) LDS_LAUNCH(es_inc_fill_kernel, grid_for(np, DB), DB, 0, s, pptr.get(), pidx.get(), np, vptr.get(),
+                       cursor.get(), vinc.get());
+    // divide and conquer: at the ratio rho_0 = |P_F| / |F| of a sub-problem, the largest
+    // maximiser of |P_F(X)| - rho_0 |X| is {x in F : phi(x) >= rho_0}.  Its value is 0
+    // exactly when F is one level (every phi = rho_0, the mean of phi over F); otherwise
+    // it is a proper nonempty subset, settled before the rest of F (highest first).
+    DevBuf<uint8_t> state(std::max(n, 1), s), side(std::max(n, 1), s);
+    DevBuf<int32_t> freeidx(std::max(n, 1), s);
+    phin.alloc(std::max(n, 1), s);
+    phid.alloc(std::max(n, 1), s);
+    LDS_CUDA(cudaMemsetAsync(state.get(), ES_BELOW, std::max(n, 1), s));
+    struct Sub {
+        std::shared_ptr<DevBuf<int32_t>> list;
+        int32_t size;
+    };
+    std::vector<Sub> todo;
+    {
+        auto l0 = std::make_shared<DevBuf<int32_t>>(std::max(n, 1), s);
+        if (n) LDS_LAUNCH(es_iota_kernel, grid_for(n, DB), DB, 0, s, l0->get(), n);
+        if (n) todo.push_back({l0, n});
     }
+    const int64_t max_subs = 2 * (int64_t)n + 2;
+    int64_t subs = 0;
+    while (!todo.empty()) {
+        Sub F = todo.back();
+        todo.pop_back();
+        ++subs;
+        LDS_REQUIRE(subs <= max_subs, LDS_ETIMEOUT, "exact settle: decomposition did not terminate");
+        const int32_t nf = F.size;
+        const int32_t* Fp = F.list->get();
+        LDS_LAUNCH(es_enter_kernel, grid_for(nf, DB), DB, 0, s, Fp, nf, state.get(), freeidx.get());
+        DevBuf<int32_t> cnt(nf + 1, s);
+        DevBuf<int64_t> off(nf + 1, s);
+        LDS_CUDA(cudaMemsetAsync(cnt.get() + nf, 0, sizeof(int32_t), s));
+        LDS_LAUNCH(es_emit_kernel<false>, grid_for((int64_t)nf * 32, DB), DB, 0, s, Fp, nf, vptr.get(), vinc.get(),
+                   pptr.get(), pidx.get(), state.get(), cnt.get(), nullptr, nullptr);
+        const int64_t nr = exclusive_scan_i32_to_i64(cnt.get(), off.get(), nf + 1, s);
+        int64_t p = 0, q = 1;
+        bool leaf = nr == 0;                      // no pattern: every phi in F is 0
+        if (!leaf) {
+            DevBuf<int32_t> pats(nr, s), len(nr + 1, s);
+            LDS_LAUNCH(es_emit_kernel<true>, grid_for((int64_t)nf * 32, DB), DB, 0, s, Fp, nf, vptr.get(), vinc.get(),
+                       pptr.get(), pidx.get(), state.get(), nullptr, off.get(), pats.get());
+            LDS_CUDA(cudaMemsetAsync(len.get() + nr, 0, sizeof(int32_t), s));
+            LDS_LAUNCH(es_len_kernel, grid_for(nr, DB), DB, 0, s, pats.get(), nr, pptr.get(), pidx.get(), state.get(),
+                       len.get());
+            DevBuf<int64_t> dptr(nr + 1, s);
+            const int64_t rn = exclusive_scan_i32_to_i64(len.get(), dptr.get(), nr + 1, s);
+            DevBuf<int32_t> ridx(std::max<int64_t>(rn, 1), s);
+            LDS_LAUNCH(es_fill_kernel, grid_for(nr, DB), DB, 0, s, pats.get(), nr, pptr.get(), pidx.get(), state.get(),
+                       freeidx.get(), dptr.get(), ridx.get());
+            const int64_t g = std::gcd(nr, (int64_t)nf);
+            p = nr / g;
+            q = nf / g;
+            LDS_REQUIRE(nr <= (int64_t)INT32_MAX, LDS_EOVERFLOW, "exact settle: %lld patterns", (long long)nr);
+            const int64_t f = pattern_max_flow(dptr.get(), ridx.get(), (int32_t)nr, nf, p, q, nullptr, side.get(), false, s);
+            ++flows;
+            leaf = q * nr - f == 0;
+            if (!leaf) {
+                DevBuf<int32_t> sd(nf + 1, s);
+                DevBuf<int64_t> pos(nf + 1, s);
+                LDS_LAUNCH(u8_to_i32_kernel, grid_for(nf, DB), DB, 0, s, side.get(), nf, sd.get());
+                LDS_CUDA(cudaMemsetAsync(sd.get() + nf, 0, sizeof(int32_t), s));
+                const int64_t xs = exclusive_scan_i32_to_i64(sd.get(), pos.get(), nf + 1, s);
+                LDS_REQUIRE(xs > 0 && xs < nf, LDS_ETIMEOUT, "exact settle: the cut at the mean ratio did not split");
+                auto X = std::make_shared<DevBuf<int32_t>>(xs, s);
+                auto Y = std::make_shared<DevBuf<int32_t>>(nf - xs, s);
+                LDS_LAUNCH(es_split_kernel, grid_for(nf, DB), DB, 0, s, Fp, nf, sd.get(), pos.get(), X->get(), Y->get());
+                LDS_LAUNCH(es_leave_kernel, grid_for(nf, DB), DB, 0, s, Fp, nf, state.get(), ES_BELOW, 0, 1, phin.get(),
+                           phid.get());
+                todo.push_back({Y, (int32_t)(nf - xs)});
+                todo.push_back({X, (int32_t)xs});
+                LDS_CUDA(cudaStreamSynchronize(s));
+                continue;
+            }
+        }
+        LDS_LAUNCH(es_leave_kernel, grid_for(nf, DB), DB, 0, s, Fp, nf, state.get(), ES_ABOVE, p, q, phin.get(),
+                   phid.get());
+        LDS_CUDA(cudaStreamSynchronize(s));
+    }
+    return flows;
+}
+
+void Driver::exact_settle(const int32_t* comp, int32_t csize) {
+    ++stats.exact_settled;
+    cudaStream_t s = st();
+    lds_graph* h = subgraph(G, comp, csize, sc);
+    struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+    const int32_t n = h->n;
+    DevBuf<int32_t> all;
+    DevBuf<int64_t> phin, phid;
+    vst.flows += exact_compact_numbers(h, tri, all, phin, phid);
     // LDSs of G[comp]: components of level sets with no neighbour of higher phi inside comp
-    std::vector<std::pair<int64_t, int64_t>> levels;
-    for (int32_t x = 0; x < n; ++x) levels.push_back({phin[x], phid[x]});
-    std::sort(levels.begin(), levels.end());
-    levels.erase(std::unique(levels.begin(), levels.end()), levels.end());
+    DevBuf<uint8_t> hflag(std::max(n, 1), s);
+    if (n) LDS_LAUNCH(es_higher_kernel, grid_for((int64_t)n * 32, DB), DB, 0, s, all.get(), n, h->nact, h->rowptr.get(),
+                      h->col.get(), h->to_orig.get(), phin.get(), phid.get(), hflag.get());
+    std::vector<int64_t> hn(n), hd(n);
+    std::vector<uint8_t> hf(n);
     std::vector<int32_t> hcomp(csize);
+    LDS_CUDA(cudaMemcpyAsync(hn.data(), phin.get(), n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaMemcpyAsync(hd.data(), phid.get(), n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LDS_CUDA(cudaMemcpyAsync(hf.data(), hflag.get(), n, cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaMemcpyAsync(hcomp.data(), comp, csize * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
-    for (auto& lv : levels) {
-        if (lv.first == 0 && !include_zero) continue;
-        std::vector<int32_t> memb;
-        for (int32_t x = 0; x < n; ++x)
-            if (phin[x] == lv.first && phid[x] == lv.second) memb.push_back(hcomp[x]);
-        DevBuf<int32_t> dm(memb.size(), s);
-        copy_in(dm.get(), memb.data(), LDS_MEM_HOST, memb.size() * sizeof(int32_t), s);
-        DevBuf<int32_t> cm;
-        std::vector<int32_t> cs;
-        components(G, dm.get(), (int32_t)memb.size(), sc, cm, cs);
-        for (size_t c = 0; c + 1 < cs.size(); ++c) {
-            int64_t npat = 0;
-            const int32_t* cp = cm.get() + cs[c];
-            int32_t csz = cs[c + 1] - cs[c];
-            if (is_densest(G, tri, cp, csz, sc, &npat)) certify(cp, csz, npat);
+    // levels holding a vertex with no higher neighbour (the others hold no LDS)
+    std::vector<std::pair<std::pair<int64_t, int64_t>, int32_t>> byl;     // ((num, den), local id)
+    for (int32_t x = 0; x < n; ++x) {
+        const int64_t g = std::gcd(hn[x], hd[x]);
+        byl.push_back({{hn[x] / (g ? g : 1), hd[x] / (g ? g : 1)}, x});
+    }
+    std::sort(byl.begin(), byl.end());
+    std::unordered_map<int32_t, int32_t> local;            // G internal id -> local id
+    for (size_t a0 = 0; a0 < byl.size();) {
+        size_t a1 = a0;
+        bool any_free = false;
+        while (a1 < byl.size() && byl[a1].first == byl[a0].first) any_free |= !hf[byl[a1++].second];
+        const auto lv = byl[a0].first;
+        if (any_free && (lv.first != 0 || include_zero)) {
+            std::vector<int32_t> memb;
+            for (size_t t = a0; t < a1; ++t) {
+                memb.push_back(hcomp[byl[t].second]);
+                local[hcomp[byl[t].second]] = byl[t].second;
+            }
+            DevBuf<int32_t> dm(memb.size(), s);
+            copy_in(dm.get(), memb.data(), LDS_MEM_HOST, memb.size() * sizeof(int32_t), s);
+            DevBuf<int32_t> cm;
+            std::vector<int32_t> cs;
+            components(G, dm.get(), (int32_t)memb.size(), sc, cm, cs);
+            std::vector<int32_t> hm(cs.back());
+            LDS_CUDA(cudaMemcpyAsync(hm.data(), cm.get(), hm.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            LDS_CUDA(cudaStreamSynchronize(s));
+            for (size_t c = 0; c + 1 < cs.size(); ++c) {
+                bool ok = true;
+                for (int32_t t = cs[c]; t < cs[c + 1] && ok; ++t) ok = !hf[local[hm[t]]];
+                if (!ok) continue;
+                int64_t npat = 0;
+                const int32_t* cp = cm.get() + cs[c];
+                const int32_t csz = cs[c + 1] - cs[c];
+                if (is_densest(G, tri, cp, csz, sc, &npat)) certify(cp, csz, npat);
+            }
         }
+        a0 = a1;
     }
 }
 
@@ -751,6 +909,20 @@ lds_status lds_topk_last_stats(lds_topk_stats_t* st) {
     return guard([&] {
         LDS_REQUIRE(st, LDS_EINVAL, "lds_topk_last_stats: NULL argument");
         *st = t_last_stats;
+    });
+}
+
+lds_status lds_compact_numbers(lds_graph* g, lds_density d, int64_t* num, int64_t* den, lds_mem where) {
+    return guard([&] {
+        LDS_REQUIRE(g && num && den, LDS_EINVAL, "lds_compact_numbers: NULL argument");
+        LDS_REQUIRE(d == LDS_EDGE || d == LDS_TRIANGLE, LDS_EINVAL, "lds_compact_numbers: bad density");
+        if (g->n == 0) return;
+        DevBuf<int32_t> all;
+        DevBuf<int64_t> phin, phid;
+        exact_compact_numbers(g, d == LDS_TRIANGLE, all, phin, phid);
+        copy_out(num, where, phin.get(), g->n * sizeof(int64_t), g->stream);
+        copy_out(den, where, phid.get(), g->n * sizeof(int64_t), g->stream);
+        LDS_CUDA(cudaStreamSynchronize(g->stream));
     });
 }
 

@@ -99,6 +99,7 @@ def load():
     _sig(lib, "lds_list_triangles", ctypes.c_int, [P, ctypes.POINTER(i64)])
     _sig(lib, "lds_get_triangles", ctypes.c_int, [P, P, ctypes.c_int])
     _sig(lib, "lds_core_numbers", ctypes.c_int, [P, ctypes.c_int, P, ctypes.c_int])
+    _sig(lib, "lds_compact_numbers", ctypes.c_int, [P, ctypes.c_int, P, P, ctypes.c_int])
     _sig(lib, "lds_fw", ctypes.c_int, [P, ctypes.c_int, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(FwResult)])
     _sig(lib, "lds_fw_last_timing", ctypes.c_int, [P, ctypes.POINTER(ctypes.c_double),
                                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -165,7 +166,7 @@ def set_pass_profiling(on: bool):
 
 
 def set_fw_variant(variant: int):
-    """0: automatic (degree-oriented pass when the keys fit); 1: symmetric-CSR pass."""
+    """0: automatic; 1-6 force one kernel form (lds_set_fw_variant in include/lds.h)."""
     _check(load().lds_set_fw_variant(int(variant)))
 
 
@@ -390,6 +391,14 @@ class Graph:
         out = np.empty(self.n, dtype=np.int64)
         _check(load().lds_core_numbers(self._h, DENSITY[density], _ptr(out), MEM_HOST))
         return out
+
+    def compact_numbers(self, density: str = "edge"):
+        """Exact compact numbers (tr-compact for "triangle"): (num, den) int64
+        arrays over the vertices, reduced fractions."""
+        num = np.empty(self.n, dtype=np.int64)
+        den = np.empty(self.n, dtype=np.int64)
+        _check(load().lds_compact_numbers(self._h, DENSITY[density], _ptr(num), _ptr(den), MEM_HOST))
+        return num, den
 
     def fw(self, iters: int, density: str = "edge", precision: str = "exact",
            want=("r", "R", "W", "last")):

@@ -84,7 +84,8 @@ def test_degenerate_graphs(lds):
             assert g.triangles().shape == (0, 3)
 
 
-@pytest.fixture(params=[0, 1, 2, 3, 4], ids=["oriented32_coop", "symmetric", "oriented64", "oriented32", "oriented32_rows"])
+@pytest.fixture(params=[0, 1, 2, 3, 4, 5, 6], ids=["auto", "symmetric", "oriented64", "oriented32", "oriented32_rows",
+                                                  "oriented32_coop", "cluster_any_size"])
 def variant(request, lds):
     lds.set_fw_variant(request.param)
     yield request.param

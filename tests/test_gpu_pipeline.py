@@ -277,3 +277,43 @@ def test_topk_planted_gnp_workload(lds):
         assert _as_lists(g.topk(5, "edge", 200, "exact")) == want
         stats = lds.topk_last_stats()
         assert stats["certified"] >= len(want)
+
+
+def _fracs(num, den):
+    return [Fraction(int(a), int(b)) for a, b in zip(num, den)]
+
+
+@pytest.mark.parametrize("seed", range(10))
+@pytest.mark.parametrize("triangle", [False, True])
+def test_compact_numbers_small_match_oracle(lds, seed, triangle):
+    # exact phi (Def. 4 / Def. 10) against the brute-force definition: the
+    # minimum over subsets of the marginal densities, all subsets enumerated
+    from oracle import brute
+    n, u, v = synth.gnp_planted(9 + seed % 4, 0.25 + 0.05 * (seed % 5), seed=14000 + seed)[:3]
+    want = brute.brute_phi(n, u, v, triangle=triangle)
+    with lds.Graph(n, u, v) as g:
+        num, den = g.compact_numbers("triangle" if triangle else "edge")
+    assert all(np.gcd(num, den) == 1) and all(den >= 1)
+    assert _fracs(num, den) == [want[x] for x in range(n)]
+
+
+@pytest.mark.parametrize("triangle", [False, True])
+def test_compact_numbers_many_levels_match_oracle(lds, triangle):
+    # a power-law graph with planted blocks: 45 edge levels and 60 triangle levels,
+    # so the divide and conquer splits many times
+    from oracle import decomp
+    n, u, v = synth.chung_lu(1500, 6000, 2.1, seed=83, n_blocks=3, block_size_range=(10, 30))[:3]
+    cu, cv = ograph.canonical_edges(n, u, v)
+    pats = ([tuple(t) for t in ograph.triangles(n, cu, cv).reshape(-1, 3).tolist()] if triangle
+            else list(zip(cu, cv)))
+    want = decomp.compact_numbers(n, pats)
+    assert len(set(want.values())) > 40
+    a, b = synth.scramble(n, u, v, seed=84)
+    with lds.Graph(n, a, b) as g:
+        num, den = g.compact_numbers("triangle" if triangle else "edge")
+    assert _fracs(num, den) == [want[x] for x in range(n)]
+    # the LDSs (LTDSs) these levels determine are what the driver certifies
+    truth = decomp.lds_from_phi(want, ograph.adjacency(n, cu, cv))
+    with lds.Graph(n, a, b) as g:
+        got = _as_lists(g.topk(6, "triangle" if triangle else "edge", 100))
+    assert got == [(d, c) for d, c in truth[:6]]

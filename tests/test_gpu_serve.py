@@ -83,6 +83,11 @@ def test_autotune_picks_a_tried_count(lds):
     gs = _graphs(lds, 8, seed=403)
     w = lds.batch_autotune([(g, 3, d, 40, "fp32") for g, d in gs])
     assert w in (1, 2, 4, 8, 16)
+    # the batched FW's launch shape was tuned for the size buckets of the edge queries
+    for g, d in gs:
+        if d == "edge":
+            info = g.info()
+            assert lds.fw_batch_threads(info["n"] - info["isolated"]) in (128, 256, 512, 1024)
     for g, _ in gs:
         g.close()
 
