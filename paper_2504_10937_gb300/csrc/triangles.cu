@@ -133,13 +133,6 @@ __global__ void tri_rows_orig_kernel(const int32_t* ta, const int32_t* tb, const
 
 // ---- peeling
 
-
-__global__ void degree_kernel(const int64_t* rowptr, int32_t nact, int32_t* deg) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
-        deg[x] = (int32_t)(rowptr[x + 1] - rowptr[x]);
-}
-
 __global__ void vt_count_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri, int32_t* cnt) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
@@ -268,17 +261,21 @@ constexpr int PEEL_CHUNK = 128;     // otherwise a warp removes each chunk of th
 // small levels of the dense tail.
 // ctrl: [0..1] frontier counts, [2] smallest kept count, [3] error (bound hit),
 // [4..5] live-list counts, [6..7] steps and last level (reported at the end),
-// [8] chunk count.  Every thread follows the same k and the same branches: the
-// counters are read right after a barrier.
+// [8] chunk count; they move to shared memory when block 0 goes on alone.  Every
+// thread follows the same k and the same branches: the counters are read right
+// after a barrier.
 __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int64_t* rowptr, const int32_t* col,
                                                             const int64_t* vptr, const int32_t* vtri,
                                                             const int32_t* ta, const int32_t* tb, const int32_t* tc,
                                                             uint8_t* tdead, uint8_t* alive, int32_t* deg,
                                                             int64_t* core, int32_t* F0, int32_t* F1, int32_t* A0,
                                                             int32_t* A1, int32_t* qv, int64_t* qs,
-                                                            unsigned long long* ctrl, int64_t max_steps,
+                                                            unsigned long long* gctrl, int64_t max_steps,
                                                             int64_t solo) {
     cg::grid_group grid = cg::this_grid();
+    // control words: global while the grid works, in shared memory once block 0 is alone
+    __shared__ unsigned long long sctrl[9];
+    unsigned long long* ctrl = gctrl;
     bool whole = true;                       // all blocks take part (grid barriers)
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -288,6 +285,9 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         if (whole) grid.sync();
         else __syncthreads();
     };
+    auto rd = [&](int i) -> unsigned long long {
+        return whole ? __ldcg(gctrl + i) : static_cast<volatile unsigned long long*>(sctrl)[i];
+    };
     const int64_t* ptr = tri ? vptr : rowptr;
     const int32_t* adj = tri ? vtri : col;
     auto F = [&](int i) { return i ? F1 : F0; };
@@ -296,10 +296,10 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
     int64_t k = 0, steps = 0;
     for (;;) {
         if (++steps > max_steps) {
-            if (tid == 0) ctrl[3] = 1;
+            if (tid == 0) gctrl[3] = 1;
             return;
         }
-        const int64_t na = (int64_t)__ldcg(ctrl + 4 + a);
+        const int64_t na = (int64_t)rd(4 + a);
         if (whole && na <= solo) {
             if (blockIdx.x != 0) return;
             whole = false;
@@ -307,6 +307,9 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
             nthreads = blockDim.x;
             warp = tid >> 5;
             nwarps = nthreads >> 5;
+            if (threadIdx.x < 9) sctrl[threadIdx.x] = __ldcg(gctrl + threadIdx.x);
+            __syncthreads();
+            ctrl = sctrl;
         }
         // level scan, warp by warp: one atomic per warp for each list and for the minimum
         for (int64_t base = tid - lane; base < na; base += nthreads) {
@@ -342,9 +345,9 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
             if (keep) A(1 - a)[kb + __popc(km & below)] = x;
         }
         barrier();
-        unsigned long long f = __ldcg(ctrl + cur);
-        const unsigned long long kept = __ldcg(ctrl + 5 - a);
-        const unsigned long long mn = __ldcg(ctrl + 2);
+        unsigned long long f = rd(cur);
+        const unsigned long long kept = rd(5 - a);
+        const unsigned long long mn = rd(2);
         barrier();
         if (tid == 0) {
             ctrl[4 + a] = 0;
@@ -354,8 +357,8 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         if (f == 0) {
             if (kept == 0) {
                 if (tid == 0) {
-                    ctrl[6] = (unsigned long long)steps;
-                    ctrl[7] = (unsigned long long)k;
+                    gctrl[6] = (unsigned long long)steps;
+                    gctrl[7] = (unsigned long long)k;
                 }
                 return;
             }
@@ -366,7 +369,7 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         // frontier rounds at level k
         while (f > 0) {
             if (++steps > max_steps) {
-                if (tid == 0) ctrl[3] = 1;
+                if (tid == 0) gctrl[3] = 1;
                 return;
             }
             int32_t* fr = F(cur);
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
                 }
             }
             barrier();
-            const int64_t nq = (int64_t)__ldcg(ctrl + 8);
+            const int64_t nq = (int64_t)rd(8);
             for (int64_t c = warp; c < nq; c += nwarps) {
                 const int32_t x = __ldcg(qv + c);
                 const int64_t q0 = __ldcg(qs + c);
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
                     }
             }
             barrier();
-            f = __ldcg(ncnt);
+            f = rd(1 - cur);
             barrier();
             if (tid == 0) {
                 ctrl[cur] = 0;
