@@ -419,6 +419,18 @@ lds_status lds_set_fw_variant(int32_t variant);
  * side.  Errors: LDS_EINVAL. */
 lds_status lds_set_flow_variant(int32_t variant);
 
+/* ExtractSG walk (Alg. 2's merge loop) for lds_extract_sg and lds_topk
+ * (process-wide):
+ *   0  automatic: graphs of at most 65,536 vertices run every single-candidate
+ *      check at once and then the whole walk in one CTA; larger graphs run the
+ *      walk on the host, single checks in growing batches, and each chain of
+ *      merged candidates on the device in one launch (running extremes of X
+ *      and S, chunk maxima of Z, chunk minima of S recomputed where they
+ *      changed);
+ *   1  the large-graph walk at every size.
+ * Both give the same groups and bounds.  Errors: LDS_EINVAL. */
+lds_status lds_set_extract_variant(int32_t variant);
+
 /* Number of CUDA kernels this library has launched since it was loaded
  * (process-wide counter; never fails). */
 int64_t lds_launch_count(void);

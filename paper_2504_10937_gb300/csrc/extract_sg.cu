@@ -25,6 +25,7 @@
 // 5. Accepted groups give lo = min_S R', hi = max_S R' (over the denominator D);
 //    by Lemma 4 / Lemma 8 lo <= D phi(u) <= hi for u in the group.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <climits>
 #include <cstdio>
@@ -376,18 +377,265 @@ __device__ __forceinline__ void chain_incidence(bool tri, int64_t p, int64_t r, 
         if (dn[j] != dold[j]) atomicAdd(delta + pp[j], (unsigned long long)(dn[j] - dold[j]));
 }
 
-__global__ void chain_extend_kernel(bool tri, const int32_t* order, const int32_t* pos, int64_t a, int64_t b0,
-                                    int64_t b1, const int64_t* ioff, int64_t ninc, const int64_t* rowptr,
-                                    const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
-                                    const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta,
-                                    const int32_t* tb, const int32_t* tc, const int64_t* W, int64_t Dn,
-                                    unsigned long long* delta) {
+// ---- one chain of merged candidates walked on the device (graphs of any size).
+// Positions in chunks of CW_CHUNK, chunks in super-chunks of CW_SUPER.  Along a
+// chain with fixed start a, X = [0, a) loads only fall, the loads of S members
+// already in S only rise and Z loads only rise (pattern_delta moves weight from
+// X to S or Z and from S to Z only), so min X and max S are running extremes, max
+// Z is a chunk maximum kept by atomics (plus the partial chunk after b), and min S
+// is recomputed only for chunks that changed.
+constexpr int CW_CHUNK = 256;
+constexpr int CW_SUPER = 256;
+
+// chunk c of S changed: listed once until its minimum is recomputed (dirty is
+// padded to whole 32-bit words)
+__device__ __forceinline__ void mark_dirty(int64_t c, uint8_t* dirty, int32_t* dlist, int32_t* nd) {
+    unsigned int* word = reinterpret_cast<unsigned int*>(dirty + (c & ~3ll));
+    const unsigned int bit = 1u << (8 * (c & 3));
+    if (!(atomicOr(word, bit) & bit)) dlist[atomicAdd(nd, 1)] = (int32_t)c;
+}
+
+// chain_incidence, also keeping the extremes: X -> running min, old S -> running
+// max and a dirty chunk, Z -> chunk and super-chunk maxima
+__device__ __forceinline__ void chain_track(bool tri, int64_t p, int64_t r, const int32_t* order, const int32_t* pos,
+                                            int64_t a, int64_t b0, int64_t b1, const int64_t* rowptr,
+                                            const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
+                                            const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta,
+                                            const int32_t* tb, const int32_t* tc, const int64_t* W, int64_t Dn,
+                                            const int64_t* R, unsigned long long* delta, unsigned long long* minX,
+                                            unsigned long long* maxS, unsigned long long* cZ, unsigned long long* sZ,
+                                            uint8_t* dirty, int32_t* dlist, int32_t* nd) {
+    const int32_t x = order[p];
+    int k;
+    int64_t pp[3], w[3];
+    if (tri) {
+        const int32_t t = vt_idx[vt_ptr[x] + r];
+        const int32_t v[3] = {ta[t], tb[t], tc[t]};
+        k = 3;
+        for (int j = 0; j < 3; ++j) {
+            pp[j] = pos[v[j]];
+            w[j] = W[3 * (int64_t)t + j];
+        }
+    } else {
+        const int64_t q = rowptr[x] + r;
+        const int32_t y = col[q];
+        const int64_t ed = slot_edge[q];
+        k = 2;
+        pp[0] = p;
+        pp[1] = pos[y];
+        w[0] = (eu[ed] == x) ? W[ed] : Dn - W[ed];
+        w[1] = Dn - w[0];
+    }
+    int64_t best = -1;
+    for (int j = 0; j < k; ++j)
+        if (pp[j] > b0 && pp[j] <= b1 && pp[j] > best) best = pp[j];
+    if (best != p) return;
+    int64_t dn[3], dold[3];
+    pattern_delta(k, pp, w, a, b1, dn);
+    pattern_delta(k, pp, w, a, b0, dold);
+    for (int j = 0; j < k; ++j) {
+        if (dn[j] == dold[j]) continue;
+        const int64_t q = pp[j];
+        const unsigned long long ch = (unsigned long long)(dn[j] - dold[j]);
+        const unsigned long long v = (unsigned long long)R[order[q]] + atomicAdd(delta + q, ch) + ch;
+        if (q < a) {
+            atomicMin(minX, v);
+        } else if (q <= b0) {
+            atomicMax(maxS, v);
+            mark_dirty(q / CW_CHUNK, dirty, dlist, nd);
+        } else if (q > b1) {
+            atomicMax(cZ + q / CW_CHUNK, v);
+            atomicMax(sZ + q / ((int64_t)CW_CHUNK * CW_SUPER), v);
+        }
+    }
+}
+
+// Chain state kept in device memory between launches (cws, 8 words): [0] min X,
+// [1] max S (running), [2] listed dirty chunks, [3] end b of S, [4] next
+// candidate, [5] 1 when that candidate's patterns are already applied, [6] steps,
+// [7] 1 once the chunk maxima of Z are set up.
+constexpr int64_t CW_HEAVY = 65536;   // a step with more incidences runs grid-wide
+
+// One chain of merged candidates with start a (S = [a, cb[k]] for k = cws[4],
+// cws[4] + 1, ...), in one CTA: stops at the first candidate whose two checks
+// pass (status 0), at the first X-side failure (status 1), after the last
+// candidate (status 2), or before a step with more than CW_HEAVY incidences
+// (status 3: the host applies them grid-wide, chain_heavy_kernel, and launches
+// this kernel again).  The caller clears delta and dirty once per chain.
+// out = {k_end, status, minS, maxS, minX, maxZ}.
+__global__ void __launch_bounds__(1024) chain_walk_kernel(
+    bool tri, const int32_t* order, const int32_t* pos, int32_t n, int32_t nact, int64_t a, int32_t ncand,
+    const int64_t* cb, const int64_t* R, const int64_t* rowptr, const int32_t* col, const int64_t* slot_edge,
+    const int32_t* eu, const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta, const int32_t* tb,
+    const int32_t* tc, const int64_t* W, int64_t Dn, unsigned long long* delta, unsigned long long* csmin,
+    unsigned long long* cZ, unsigned long long* sZ, uint8_t* dirty, int32_t* dlist, long long* cws, long long* out) {
+    __shared__ unsigned long long s_minX, s_maxS;
+    __shared__ unsigned long long red[2][32];
+    __shared__ long long s_cnt;
+    __shared__ int32_t s_nd, s_done;
+    const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = bd >> 5;
+    const int64_t nchunks = ((int64_t)n + CW_CHUNK - 1) / CW_CHUNK;
+    const int64_t nsuper = (nchunks + CW_SUPER - 1) / CW_SUPER;
+    if (cws[7] == 0) {
+        // unmodified maxima: the first position of a chunk holds its largest load
+        for (int64_t c = tid; c < nchunks; c += bd) cZ[c] = (unsigned long long)R[order[c * CW_CHUNK]];
+        for (int64_t c = tid; c < nsuper; c += bd) sZ[c] = (unsigned long long)R[order[c * CW_CHUNK * CW_SUPER]];
+    }
+    if (tid == 0) {
+        const bool first = cws[7] == 0;
+        s_minX = first ? (a > 0 ? (unsigned long long)R[order[a - 1]] : ~0ull) : (unsigned long long)cws[0];
+        s_maxS = first ? 0ull : (unsigned long long)cws[1];
+        s_nd = first ? 0 : (int32_t)cws[2];
+        s_done = 0;
+    }
+    __syncthreads();
+    int64_t b = cws[3], steps = cws[6];
+    bool applied = cws[5] != 0;
+    int32_t k = (int32_t)cws[4];
+    for (; k < ncand; ++k) {
+        const int64_t b0 = b, b1 = cb[k];
+        if (!applied) {
+            // incidences of the added positions: past CW_HEAVY the grid takes them
+            if (tid == 0) s_cnt = 0;
+            __syncthreads();
+            long long c = 0;
+            for (int64_t p = b0 + 1 + tid; p <= b1; p += bd) {
+                const int32_t x = order[p];
+                if (x < nact) c += tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
+            }
+            for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0 && c) atomicAdd(reinterpret_cast<unsigned long long*>(&s_cnt), (unsigned long long)c);
+            __syncthreads();
+            if (s_cnt > CW_HEAVY) {
+                if (tid == 0) {
+                    cws[0] = (long long)s_minX;
+                    cws[1] = (long long)s_maxS;
+                    cws[2] = s_nd;
+                    cws[3] = b;
+                    cws[4] = k;
+                    cws[5] = 0;
+                    cws[6] = steps;
+                    cws[7] = 1;
+                    out[1] = 3;
+                }
+                return;
+            }
+            // one position by the whole block, several by one warp each
+            if (b1 == b0 + 1) {
+                const int32_t x = order[b1];
+                if (x < nact) {
+                    const int64_t deg = tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
+                    for (int64_t r = tid; r < deg; r += bd)
+                        chain_track(tri, b1, r, order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx, ta,
+                                    tb, tc, W, Dn, R, delta, &s_minX, &s_maxS, cZ, sZ, dirty, dlist, &s_nd);
+                }
+            } else {
+                for (int64_t p = b0 + 1 + wid; p <= b1; p += nw) {
+                    const int32_t x = order[p];
+                    if (x >= nact) continue;
+                    const int64_t deg = tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
+                    for (int64_t r = lane; r < deg; r += 32)
+                        chain_track(tri, p, r, order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx, ta,
+                                    tb, tc, W, Dn, R, delta, &s_minX, &s_maxS, cZ, sZ, dirty, dlist, &s_nd);
+                }
+            }
+        }
+        applied = false;
+        for (int64_t p = b0 + 1 + tid; p <= b1; p += bd)
+            if (p == b0 + 1 || p % CW_CHUNK == 0) mark_dirty(p / CW_CHUNK, dirty, dlist, &s_nd);
+        __syncthreads();
+        // the new members' loads, and the minima of the changed chunks of S
+        for (int64_t p = b0 + 1 + tid; p <= b1; p += bd)
+            atomicMax(&s_maxS, (unsigned long long)R[order[p]] + delta[p]);
+        const int32_t nd = s_nd;
+        for (int32_t i = wid; i < nd; i += nw) {
+            const int64_t c = dlist[i];
+            const int64_t lo = max(c * CW_CHUNK, a), hi = min(c * CW_CHUNK + CW_CHUNK - 1, b1);
+            unsigned long long m = ~0ull;
+            for (int64_t p = lo + lane; p <= hi; p += 32) m = min(m, (unsigned long long)R[order[p]] + delta[p]);
+            for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) {
+                csmin[c] = m;
+                dirty[c] = 0;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_nd = 0;
+        // min S over its chunks; max Z over the rest of b's chunk, the chunks to the
+        // end of its super-chunk and the super-chunks after
+        unsigned long long mS = ~0ull, mZ = 0;
+        for (int64_t c = a / CW_CHUNK + tid; c <= b1 / CW_CHUNK; c += bd) mS = min(mS, csmin[c]);
+        if (b1 < n - 1) {
+            const int64_t cz = b1 / CW_CHUNK, sz = cz / CW_SUPER;
+            const int64_t pend = min((int64_t)n, (cz + 1) * CW_CHUNK);
+            for (int64_t p = b1 + 1 + tid; p < pend; p += bd)
+                mZ = max(mZ, (unsigned long long)R[order[p]] + delta[p]);
+            const int64_t cend = min(nchunks, (sz + 1) * CW_SUPER);
+            for (int64_t c = cz + 1 + tid; c < cend; c += bd) mZ = max(mZ, cZ[c]);
+            for (int64_t c = sz + 1 + tid; c < nsuper; c += bd) mZ = max(mZ, sZ[c]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            mS = min(mS, __shfl_xor_sync(0xffffffffu, mS, o));
+            mZ = max(mZ, __shfl_xor_sync(0xffffffffu, mZ, o));
+        }
+        if (lane == 0) {
+            red[0][wid] = mS;
+            red[1][wid] = mZ;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int j = 1; j < nw; ++j) {
+                mS = min(mS, red[0][j]);
+                mZ = max(mZ, red[1][j]);
+            }
+            ++steps;
+            const long long lo = (long long)mS, hi = (long long)s_maxS;
+            const long long mx = s_minX == ~0ull ? LLONG_MAX : (long long)s_minX;
+            const long long mz = b1 == n - 1 ? LLONG_MIN : (long long)mZ;
+            const bool xok = a == 0 || mx > hi;
+            const bool zok = b1 == n - 1 || mz < lo;
+            if (!xok || zok) {
+                out[0] = k;
+                out[1] = xok ? 0 : 1;
+                out[2] = lo;
+                out[3] = hi;
+                out[4] = mx;
+                out[5] = mz;
+                s_done = 1;
+            }
+        }
+        __syncthreads();
+        if (s_done) break;
+        b = b1;
+    }
+    if (tid == 0) {
+        if (!s_done) {
+            out[0] = ncand;
+            out[1] = 2;
+        }
+        cws[6] = steps;
+    }
+}
+
+// the patterns of positions (b0, b1] of a chain grid-wide: one work item per
+// incidence, the same tracking as in chain_walk_kernel, the running extremes
+// and the dirty count in cws
+__global__ void chain_heavy_kernel(bool tri, const int32_t* order, const int32_t* pos, int64_t a, int64_t b0, int64_t b1,
+                                   const int64_t* ioff, int64_t ninc, const int64_t* rowptr, const int32_t* col,
+                                   const int64_t* slot_edge, const int32_t* eu, const int64_t* vt_ptr,
+                                   const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+                                   const int64_t* W, int64_t Dn, const int64_t* R, unsigned long long* delta,
+                                   unsigned long long* cZ, unsigned long long* sZ, uint8_t* dirty, int32_t* dlist,
+                                   long long* cws) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int32_t plo = (int32_t)(b0 + 1), phi = (int32_t)(b1 + 1);
+    unsigned long long* gX = reinterpret_cast<unsigned long long*>(cws);
+    unsigned long long* gS = reinterpret_cast<unsigned long long*>(cws + 1);
+    int32_t* gnd = reinterpret_cast<int32_t*>(cws + 2);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ninc; i += stride) {
         const int64_t p = inc_position(ioff, plo, phi, i);
-        chain_incidence(tri, p, i - ioff[p - plo], order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx,
-                        ta, tb, tc, W, Dn, delta);
+        chain_track(tri, p, i - ioff[p - plo], order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx, ta,
+                    tb, tc, W, Dn, R, delta, gX, gS, cZ, sZ, dirty, dlist, gnd);
     }
 }
 
@@ -401,7 +649,7 @@ __global__ void __launch_bounds__(1024) sg_walk_small_kernel(
     const int64_t* R, const int64_t* rowptr, const int32_t* col, const int64_t* slot_edge, const int32_t* eu,
     const int64_t* vt_ptr, const int32_t* vt_idx, const int32_t* ta, const int32_t* tb, const int32_t* tc,
     const int64_t* W, int64_t Dn, unsigned long long* delta, int64_t* gend, long long* glo, long long* ghi,
-    int32_t* ngroups, int64_t* chain_checks) {
+    int32_t* ngroups, int64_t* chain_checks, bool fresh) {
     __shared__ unsigned long long red[4][32];
     __shared__ long long res[4];
     __shared__ int64_t s_start, s_a, s_b;
@@ -420,9 +668,10 @@ __global__ void __launch_bounds__(1024) sg_walk_small_kernel(
     for (int32_t k = 0; k < ncand; ++k) {
         const int64_t start = s_start;
         long long lo, hi, mx, mz;
-        if (ca[k] == start) {
+        if (ca[k] == start && !fresh) {
             lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
+            // (fresh: a single check is the first step of a chain from its start)
             if (s_a != start) {
                 for (int32_t p = tid; p < n; p += bd) delta[p] = 0;
                 __syncthreads();
@@ -490,43 +739,6 @@ __global__ void __launch_bounds__(1024) sg_walk_small_kernel(
     if (tid == 0) {
         *ngroups = s_ng;
         *chain_checks = s_checks;
-    }
-}
-
-// min / max of R + delta over X = [0, a), S = [a, b], Z = (b, n); out = {minS, maxS, minX, maxZ},
-// loads are nonnegative so unsigned atomics order them
-__global__ void chain_extremes_kernel(const int32_t* order, const int64_t* R, const int64_t* delta, int32_t n,
-                                      int64_t a, int64_t b, unsigned long long* out) {
-    __shared__ unsigned long long sh[4][32];
-    unsigned long long mnS = ~0ull, mxS = 0, mnX = ~0ull, mxZ = 0;
-    bool hasZ = false;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-        const unsigned long long v = (unsigned long long)(R[order[p]] + delta[p]);
-        if (p < a) mnX = min(mnX, v);
-        else if (p <= b) { mnS = min(mnS, v); mxS = max(mxS, v); }
-        else { mxZ = max(mxZ, v); hasZ = true; }
-    }
-    (void)hasZ;
-    for (int o = 16; o; o >>= 1) {
-        mnS = min(mnS, __shfl_xor_sync(0xffffffffu, mnS, o));
-        mxS = max(mxS, __shfl_xor_sync(0xffffffffu, mxS, o));
-        mnX = min(mnX, __shfl_xor_sync(0xffffffffu, mnX, o));
-        mxZ = max(mxZ, __shfl_xor_sync(0xffffffffu, mxZ, o));
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) { sh[0][wid] = mnS; sh[1][wid] = mxS; sh[2][wid] = mnX; sh[3][wid] = mxZ; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        for (int j = 1; j < nw; ++j) {
-            mnS = min(mnS, sh[0][j]); mxS = max(mxS, sh[1][j]);
-            mnX = min(mnX, sh[2][j]); mxZ = max(mxZ, sh[3][j]);
-        }
-        atomicMin(out + 0, mnS);
-        atomicMax(out + 1, mxS);
-        atomicMin(out + 2, mnX);
-        atomicMax(out + 3, mxZ);
     }
 }
 
@@ -725,65 +937,8 @@ static void check_segments(lds_graph* g, const SgState& st, int32_t* segof, cons
 
 // graphs up to this many vertices run the check walk in one CTA (sg_walk_small_kernel)
 constexpr int32_t kSmallWalk = 65536;
-
-// A growing segment [a, b] of one chain of merged candidates (see chain_extend_kernel).
-struct Chain {
-    lds_graph* g;
-    const SgState& st;
-    DevBuf<int64_t> delta;
-    DevBuf<unsigned long long> ext;
-    int64_t a = -1, b = -1;
-    Chain(lds_graph* gg, const SgState& s_) : g(gg), st(s_) {}
-
-    void begin(int64_t start) {
-        cudaStream_t s = g->stream;
-        const int32_t n = g->n;
-        if (!delta.p) {
-            delta.alloc(n, s);
-            ext.alloc(4, s);
-        }
-        LDS_CUDA(cudaMemsetAsync(delta.get(), 0, n * sizeof(int64_t), s));
-        a = start;
-        b = start - 1;
-    }
-
-    // grows S to [a, b1]; returns (minS, maxS, minX, maxZ) of the modified loads
-    void extend(int64_t b1, long long out[4]) {
-        cudaStream_t s = g->stream;
-        const int blk = 256;
-        const int32_t n = g->n, nact = g->nact;
-        const bool tri = g->fw_density == LDS_TRIANGLE;
-        const int32_t plo = (int32_t)(b + 1), phi = (int32_t)(b1 + 1);
-        if ((tri && g->ntri) || (!tri && g->m)) {
-            if (tri) ensure_vertex_triangles(g);
-            else ensure_slot_edge(g);
-            const int64_t* iptr = tri ? g->vt_ptr.get() : g->rowptr.get();
-            // every position in (b, b1] is walked (no segment map)
-            DevBuf<int64_t> icnt(phi - plo, s), ioff(phi - plo, s);
-            LDS_LAUNCH(inc_count_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(), (const int32_t*)nullptr,
-                       plo, phi, iptr, nact, icnt.get());
-            const int64_t ninc = exclusive_scan_i64(icnt.get(), ioff.get(), phi - plo, s);
-            if (ninc)
-                LDS_LAUNCH(chain_extend_kernel, grid_for(ninc, blk), blk, 0, s, tri, st.order.get(), st.pos.get(), a, b,
-                           b1, ioff.get(), ninc, g->rowptr.get(), g->col.get(), tri ? nullptr : g->slot_edge.get(),
-                           g->eu.get(), tri ? g->vt_ptr.get() : nullptr, tri ? g->vt_idx.get() : nullptr,
-                           g->ta.get(), g->tb.get(), g->tc.get(), g->fw_W.get(), g->fw_D,
-                           (unsigned long long*)delta.get());
-        }
-        b = b1;
-        const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
-        LDS_CUDA(cudaMemcpyAsync(ext.get(), init, sizeof(init), cudaMemcpyHostToDevice, s));
-        LDS_LAUNCH(chain_extremes_kernel, grid_for(n, blk), blk, 0, s, st.order.get(), g->fw_R.get(), delta.get(), n,
-                   a, b, ext.get());
-        unsigned long long h[4];
-        LDS_CUDA(cudaMemcpyAsync(h, ext.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
-        LDS_CUDA(cudaStreamSynchronize(s));
-        out[0] = (long long)h[0];
-        out[1] = (long long)h[1];
-        out[2] = h[2] == ~0ull ? LLONG_MAX : (long long)h[2];
-        out[3] = b == n - 1 ? LLONG_MIN : (long long)h[3];
-    }
-};
+// 0: by size; 1: the walk of large graphs (host loop, device chains) at every size
+std::atomic<int> g_sg_variant{0};
 
 void extract_sg(lds_graph* g, SgState& st) {
     LDS_REQUIRE(g->fw_valid, LDS_EINVAL, "extract_sg: run lds_fw on this graph first");
@@ -885,8 +1040,11 @@ void extract_sg(lds_graph* g, SgState& st) {
     // every longer merge, so the whole rest is the unaccepted remainder.
     // Small graphs (refinement rounds on G[C]): every single check at once, then the
     // whole walk, chains included, in one CTA.
-    if (n <= kSmallWalk && ncand > 0) {
-        ensure_checked(ncand - 1);
+    if (n <= kSmallWalk && ncand > 0 && g_sg_variant.load(std::memory_order_relaxed) == 0) {
+        // few candidates: each single check is a chain step inside the walk (one
+        // reset of the n chain deltas per start), no batched checks at all
+        const bool fresh = (int64_t)ncand * n <= ((int64_t)1 << 26);
+        if (!fresh) ensure_checked(ncand - 1);
         const bool tri_g = tri;
         if (tri_g) ensure_vertex_triangles(g);
         else if (g->m) ensure_slot_edge(g);
@@ -905,7 +1063,7 @@ void extract_sg(lds_graph* g, SgState& st) {
                    g->rowptr.get(), g->col.get(), tri_g ? nullptr : g->slot_edge.get(), g->eu.get(),
                    tri_g ? g->vt_ptr.get() : nullptr, tri_g ? g->vt_idx.get() : nullptr, g->ta.get(), g->tb.get(),
                    g->tc.get(), g->fw_W.get(), g->fw_D, delta.get(), dgend.get(), dlo.get(), dhi.get(), dng.get(),
-                   dchk.get());
+                   dchk.get(), fresh);
         int32_t ng = 0;
         int64_t chk = 0;
         LDS_CUDA(cudaMemcpyAsync(&ng, dng.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -930,9 +1088,16 @@ void extract_sg(lds_graph* g, SgState& st) {
                         ms_cuts);
         return;
     }
-    // Merged candidates of one start are checked incrementally (Chain): each step
+    // A chain of merged candidates (the single check at the start failed on the Z
+    // side) is walked on the device in one launch (chain_walk_kernel): each step
     // only walks the patterns of the positions it adds.
-    Chain chain(g, st);
+    const int64_t nchunks = ((int64_t)n + CW_CHUNK - 1) / CW_CHUNK;
+    const int64_t nsuper = (nchunks + CW_SUPER - 1) / CW_SUPER;
+    DevBuf<unsigned long long> cw_delta, cw_smin, cw_z, cw_sz;
+    DevBuf<uint8_t> cw_dirty;
+    DevBuf<int32_t> cw_list;
+    DevBuf<int64_t> cw_cb;
+    DevBuf<long long> cw_out, cw_state;
     int64_t start = 0;
     for (size_t k = 0; k < ca.size(); ++k) {
         long long lo, hi, mx, mz;
@@ -940,11 +1105,58 @@ void extract_sg(lds_graph* g, SgState& st) {
             ensure_checked(k);
             lo = mnS[k]; hi = mxS[k]; mx = mnX[k]; mz = mxZ[k];
         } else {
-            if (chain.a != start) chain.begin(start);
-            long long e[4];
-            chain.extend(cb[k], e);
-            lo = e[0]; hi = e[1]; mx = e[2]; mz = e[3];
-            ++st.chain_checks;
+            if (!cw_out.p) {
+                cw_delta.alloc(n, s);
+                cw_smin.alloc(nchunks, s);
+                cw_z.alloc(nchunks, s);
+                cw_sz.alloc(nsuper, s);
+                cw_dirty.alloc((nchunks + 3) & ~3ll, s);
+                cw_list.alloc(nchunks, s);
+                cw_cb.alloc(ca.size(), s);
+                cw_out.alloc(8, s);
+                cw_state.alloc(8, s);
+                copy_in(cw_cb.get(), cb.data(), LDS_MEM_HOST, cb.size() * sizeof(int64_t), s);
+                if (tri) ensure_vertex_triangles(g);
+                else if (g->m) ensure_slot_edge(g);
+            }
+            LDS_CUDA(cudaMemsetAsync(cw_delta.get(), 0, (size_t)n * sizeof(unsigned long long), s));
+            LDS_CUDA(cudaMemsetAsync(cw_dirty.get(), 0, (nchunks + 3) & ~3ll, s));
+            const long long init[8] = {0, 0, 0, (long long)start - 1, (long long)k, 0, 0, 0};
+            copy_in(cw_state.get(), init, LDS_MEM_HOST, sizeof(init), s);
+            long long h[8], cs[8];
+            for (;;) {
+                LDS_LAUNCH(chain_walk_kernel, 1, 1024, 0, s, tri, st.order.get(), st.pos.get(), n, g->nact, start,
+                           (int32_t)ca.size(), cw_cb.get(), g->fw_R.get(), g->rowptr.get(), g->col.get(),
+                           tri ? nullptr : g->slot_edge.get(), g->eu.get(), tri ? g->vt_ptr.get() : nullptr,
+                           tri ? g->vt_idx.get() : nullptr, g->ta.get(), g->tb.get(), g->tc.get(), g->fw_W.get(),
+                           g->fw_D, cw_delta.get(), cw_smin.get(), cw_z.get(), cw_sz.get(), cw_dirty.get(),
+                           cw_list.get(), cw_state.get(), cw_out.get());
+                LDS_CUDA(cudaMemcpyAsync(h, cw_out.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+                LDS_CUDA(cudaMemcpyAsync(cs, cw_state.get(), sizeof(cs), cudaMemcpyDeviceToHost, s));
+                LDS_CUDA(cudaStreamSynchronize(s));
+                if (h[1] != 3) break;
+                // a heavy step: its incidences grid-wide, then the walk goes on
+                const int64_t b0 = cs[3], b1 = cb[cs[4]];
+                const int32_t plo = (int32_t)(b0 + 1), phi = (int32_t)(b1 + 1);
+                const int64_t* iptr = tri ? g->vt_ptr.get() : g->rowptr.get();
+                DevBuf<int64_t> icnt(phi - plo, s), ioff(phi - plo, s);
+                LDS_LAUNCH(inc_count_kernel, grid_for(phi - plo, blk), blk, 0, s, st.order.get(),
+                           (const int32_t*)nullptr, plo, phi, iptr, g->nact, icnt.get());
+                const int64_t ninc = exclusive_scan_i64(icnt.get(), ioff.get(), phi - plo, s);
+                if (ninc)
+                    LDS_LAUNCH(chain_heavy_kernel, grid_for(ninc, blk), blk, 0, s, tri, st.order.get(), st.pos.get(),
+                               start, b0, b1, ioff.get(), ninc, g->rowptr.get(), g->col.get(),
+                               tri ? nullptr : g->slot_edge.get(), g->eu.get(), tri ? g->vt_ptr.get() : nullptr,
+                               tri ? g->vt_idx.get() : nullptr, g->ta.get(), g->tb.get(), g->tc.get(), g->fw_W.get(),
+                               g->fw_D, g->fw_R.get(), cw_delta.get(), cw_z.get(), cw_sz.get(), cw_dirty.get(),
+                               cw_list.get(), cw_state.get());
+                const long long one = 1;
+                copy_in(cw_state.get() + 5, &one, LDS_MEM_HOST, sizeof(one), s);
+            }
+            st.chain_checks += cs[6];
+            if (h[1] == 2) break;                 // no candidate left: the rest is the remainder
+            k = (size_t)h[0];
+            lo = h[2]; hi = h[3]; mx = h[4]; mz = h[5];
         }
         const bool xok = start == 0 || mx > hi;
         const bool zok = cb[k] == n - 1 || mz < lo;
@@ -967,6 +1179,13 @@ void extract_sg(lds_graph* g, SgState& st) {
 }  // namespace lds
 
 using namespace lds;
+
+extern "C" lds_status lds_set_extract_variant(int32_t variant) {
+    return guard([&] {
+        LDS_REQUIRE(variant == 0 || variant == 1, LDS_EINVAL, "lds_set_extract_variant: %d is not 0 or 1", variant);
+        g_sg_variant.store(variant, std::memory_order_relaxed);
+    });
+}
 
 extern "C" lds_status lds_extract_sg(lds_graph* g, int32_t* order, int32_t* ngroups, int64_t* group_end,
                                      int64_t* lo_num, int64_t* hi_num, int64_t* D, int32_t* ncuts, int64_t* cuts) {

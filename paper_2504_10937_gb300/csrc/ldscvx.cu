@@ -300,6 +300,36 @@ __global__ void es_higher_kernel(const int32_t* all, int32_t n, int32_t nact, co
     }
 }
 
+// component id of every member (components listed back to back, offsets off)
+__global__ void comp_id_kernel(const int32_t* cm, const int32_t* off, int32_t ncomp, int32_t* compid) {
+    const int64_t total = off[ncomp];
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        int32_t lo = 0, hi = ncomp;              // last component with off <= i
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid;
+        }
+        compid[cm[i]] = lo;
+    }
+}
+
+// one warp per member: its component is open if the member has a neighbour in G
+// outside it
+__global__ void comp_open_kernel(const int32_t* cm, int64_t total, const int32_t* compid, int32_t nact,
+                                 const int64_t* rowptr, const int32_t* col, uint8_t* open) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+        const int32_t x = cm[i];
+        if (x >= nact) continue;
+        const int32_t c = compid[x];
+        bool out = false;
+        for (int64_t e = rowptr[x] + lane; e < rowptr[x + 1] && !out; e += 32) out = compid[col[e]] != c;
+        if (__any_sync(0xffffffffu, out) && lane == 0) open[c] = 1;
+    }
+}
+
 }  // namespace
 
 struct Timers {
@@ -411,9 +441,13 @@ struct Driver {
         return true;
     }
 
-    void certify(const int32_t* comp, int32_t csize, int64_t npat) {
+    // closed: S is a whole connected component of G.  With no neighbour outside, a
+    // self-densest G[S] is rho-compact (every T in S has density <= rho, which is
+    // the compactness inequality for U = S - T) and no connected proper supergraph
+    // exists, so S is an LDS (LTDS) without a flow.
+    void certify(const int32_t* comp, int32_t csize, int64_t npat, bool closed = false) {
         if (npat == 0 && !include_zero) return;
-        bool ok = is_lds(G, tri, comp, csize, npat, bG, sc, &vst, vmode);
+        bool ok = closed || is_lds(G, tri, comp, csize, npat, bG, sc, &vst, vmode);
         if (ok) {
             Found f;
             int64_t g = std::gcd(npat, (int64_t)csize);
@@ -427,6 +461,30 @@ struct Driver {
         } else {
             ++stats.failed;
         }
+    }
+
+    // 1 for every component (listed back to back in cm, offsets cs) that is a whole
+    // connected component of G
+    std::vector<uint8_t> closed_components(const int32_t* cm, const std::vector<int32_t>& cs) {
+        cudaStream_t s = st();
+        const int32_t nc = (int32_t)cs.size() - 1;
+        std::vector<uint8_t> closed(std::max(nc, 0), 0);
+        if (nc <= 0) return closed;
+        const int64_t total = cs.back();
+        DevBuf<int32_t> off(nc + 1, s), compid(std::max(G->n, 1), s);
+        DevBuf<uint8_t> open(nc, s);
+        copy_in(off.get(), cs.data(), LDS_MEM_HOST, (nc + 1) * sizeof(int32_t), s);
+        LDS_CUDA(cudaMemsetAsync(compid.get(), 0xff, std::max(G->n, 1) * sizeof(int32_t), s));
+        LDS_CUDA(cudaMemsetAsync(open.get(), 0, nc, s));
+        if (total) {
+            LDS_LAUNCH(comp_id_kernel, grid_for(total, DB), DB, 0, s, cm, off.get(), nc, compid.get());
+            LDS_LAUNCH(comp_open_kernel, grid_for(total * 32, DB), DB, 0, s, cm, total, compid.get(), G->nact,
+                       G->rowptr.get(), G->col.get(), open.get());
+        }
+        LDS_CUDA(cudaMemcpyAsync(closed.data(), open.get(), nc, cudaMemcpyDeviceToHost, s));
+        LDS_CUDA(cudaStreamSynchronize(s));
+        for (auto& c : closed) c = !c;
+        return closed;
     }
 
     // Compact numbers of G[comp] by the density-friendly decomposition, then the
@@ -687,6 +745,7 @@ void Driver::run() {
                     std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv0).count());
         double small_ms = 0;
         int small_n = 0;
+        const std::vector<uint8_t> closed = closed_components(cm.get(), cs);
         auto cmh = std::make_shared<DevBuf<int32_t>>(std::move(cm));
         for (size_t c = 0; c + 1 < cs.size(); ++c) {
             const int32_t* comp = cmh->get() + cs[c];
@@ -706,7 +765,7 @@ void Driver::run() {
             }
             auto tv2 = std::chrono::steady_clock::now();
             if (dens) {
-                certify(comp, csize, npat);
+                certify(comp, csize, npat, closed[c] != 0);
                 auto tv3 = std::chrono::steady_clock::now();
                 tm.verify += std::chrono::duration<double, std::milli>(tv3 - tv1).count();
                 if (verbose && csize > 2)

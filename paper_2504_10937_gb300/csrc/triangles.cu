@@ -13,6 +13,7 @@
 // and is removed, its neighbours' degrees drop, and the step repeats until no
 // vertex is removed; then k moves to the smallest remaining degree.
 #include <algorithm>
+#include <climits>
 
 #include <cooperative_groups.h>
 #include <cstdio>
@@ -133,24 +134,6 @@ __global__ void tri_rows_orig_kernel(const int32_t* ta, const int32_t* tb, const
 
 // ---- peeling
 
-__global__ void vt_count_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri, int32_t* cnt) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
-        atomicAdd(cnt + ta[t], 1);
-        atomicAdd(cnt + tb[t], 1);
-        atomicAdd(cnt + tc[t], 1);
-    }
-}
-
-__global__ void vt_fill_kernel(const int32_t* ta, const int32_t* tb, const int32_t* tc, int64_t ntri,
-                               const int64_t* vptr, int32_t* cursor, int32_t* vtri) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntri; t += stride) {
-        int32_t v3[3] = {ta[t], tb[t], tc[t]};
-        for (int k = 0; k < 3; ++k) vtri[vptr[v3[k]] + atomicAdd(cursor + v3[k], 1)] = (int32_t)t;
-    }
-}
-
 __global__ void alive_init_kernel(const uint8_t* init, int32_t nact, uint8_t* alive, int64_t* core, int32_t* nalive) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int32_t c = 0;
@@ -248,6 +231,170 @@ __device__ __forceinline__ void peel_triangle(int32_t t, int32_t x, int64_t k, c
 constexpr int PEEL_LIGHT = 8;       // a lane removes a vertex with at most this many incidences
 constexpr int PEEL_CHUNK = 128;     // otherwise a warp removes each chunk of this many (4 per lane)
 
+constexpr int PEEL_SOLO = 8192;      // live vertices the one-block kernel finishes with, in shared memory
+constexpr int PEEL_SOLO_T = 1024;    // its threads
+constexpr size_t PEEL_SOLO_SMEM = 16 + (size_t)PEEL_SOLO * (4 * sizeof(int32_t) + 1);
+
+// exclusive block scan of one int64 per thread (PEEL_SOLO_T threads); returns the total
+__device__ __forceinline__ int64_t block_scan_i64(int64_t v, int64_t* out, int64_t* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;                          // inclusive warp totals
+    }
+    __syncthreads();
+    out[tid] = inc - v + (wid ? wsum[wid - 1] : 0);
+    const int64_t total = wsum[31];
+    __syncthreads();
+    return total;
+}
+
+// The dense tail of the peel, in one block, once at most PEEL_SOLO vertices are
+// live (the grid-wide kernel hands over through ctrl[9..12]).  Their counts, live
+// flags and the frontiers sit in shared memory (live vertex x at slot[x]; slot
+// is -1 for every other vertex, whose count no longer matters), so a round costs
+// block barriers and shared-memory atomics instead of grid barriers and L2
+// atomics.  A round's incidences are spread evenly over the threads (batches of
+// PEEL_SOLO_T frontier vertices, a scan of their incidence counts), so one hub
+// does not hold the round.  Same levels and rules as the grid-wide loop.
+__global__ void __launch_bounds__(PEEL_SOLO_T, 1) peel_solo_kernel(
+    bool tri, const int64_t* ptr, const int32_t* adj, const int32_t* ta, const int32_t* tb, const int32_t* tc,
+    uint8_t* tdead, const uint8_t* alive, const int32_t* deg, int64_t* core, const int32_t* A0, const int32_t* A1,
+    int32_t* slot, unsigned long long* ctrl, int64_t max_steps) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ int64_t b_off[PEEL_SOLO_T], b_beg[PEEL_SOLO_T], wsum[32];
+    __shared__ int32_t b_x[PEEL_SOLO_T];
+    if (ctrl[12] == 0) return;                  // the grid-wide kernel finished the peel
+    const int32_t* list = ctrl[9] ? A1 : A0;
+    const int32_t nl = (int32_t)ctrl[4 + ctrl[9]];
+    int64_t k = (int64_t)ctrl[10], steps = (int64_t)ctrl[11];
+    int32_t* sc = reinterpret_cast<int32_t*>(psm);              // [0] frontier count, [1] smallest kept count
+    int32_t* sv = sc + 4;                                         // vertex of each slot
+    int32_t* sd = sv + PEEL_SOLO;                                 // its count
+    int32_t* fa = sd + PEEL_SOLO;                                 // frontiers (slots)
+    int32_t* fb = fa + PEEL_SOLO;
+    uint8_t* sl = reinterpret_cast<uint8_t*>(fb + PEEL_SOLO);     // live flag
+    const int tid = threadIdx.x, bd = blockDim.x;
+    for (int i = tid; i < nl; i += bd) {
+        const int32_t x = list[i];
+        sv[i] = x;
+        sd[i] = deg[x];
+        sl[i] = alive[x];
+        slot[x] = i;
+    }
+    __syncthreads();
+    for (;;) {
+        if (++steps > max_steps) {
+            if (tid == 0) ctrl[3] = 1;
+            return;
+        }
+        if (tid == 0) {
+            sc[0] = 0;
+            sc[1] = INT_MAX;
+        }
+        __syncthreads();
+        // level scan: live vertices with count <= k are peeled at k
+        for (int i = tid; i < nl; i += bd)
+            if (sl[i]) {
+                const int32_t d = sd[i];
+                if (d <= k) {
+                    sl[i] = 0;
+                    core[sv[i]] = k;
+                    fa[atomicAdd(sc, 1)] = i;
+                } else {
+                    atomicMin(sc + 1, d);
+                }
+            }
+        __syncthreads();
+        int32_t nf = sc[0];
+        const int32_t mn = sc[1];
+        __syncthreads();
+        if (nf == 0) {
+            if (mn == INT_MAX) {
+                if (tid == 0) {
+                    ctrl[6] = (unsigned long long)steps;
+                    ctrl[7] = (unsigned long long)k;
+                }
+                return;
+            }
+            k = max(k + 1, (int64_t)mn);
+            continue;
+        }
+        int32_t* cf = fa;
+        int32_t* nx = fb;
+        while (nf > 0) {
+            if (++steps > max_steps) {
+                if (tid == 0) ctrl[3] = 1;
+                return;
+            }
+            if (tid == 0) sc[0] = 0;
+            __syncthreads();
+            // a vertex whose count falls from k + 1 to k is peeled at k
+            auto drop = [&](int32_t y) {
+                const int32_t j = slot[y];
+                if (j >= 0 && atomicSub(sd + j, 1) == k + 1) {
+                    sl[j] = 0;
+                    core[y] = k;
+                    nx[atomicAdd(sc, 1)] = j;
+                }
+            };
+            for (int32_t base = 0; base < nf; base += bd) {
+                const int32_t j = base + tid;
+                int64_t d = 0, b0 = 0;
+                int32_t x = -1;
+                if (j < nf) {
+                    x = sv[cf[j]];
+                    b0 = ptr[x];
+                    d = ptr[x + 1] - b0;
+                }
+                const int64_t total = block_scan_i64(d, b_off, wsum);
+                b_x[tid] = x;
+                b_beg[tid] = b0;
+                __syncthreads();
+                const int32_t cnt = min(bd, nf - base);
+                for (int64_t i = tid; i < total; i += bd) {
+                    int32_t lo = 0, hi = cnt;            // last entry with offset <= i
+                    while (hi - lo > 1) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (b_off[mid] <= i) lo = mid; else hi = mid;
+                    }
+                    const int32_t xv = b_x[lo];
+                    const int32_t e = adj[b_beg[lo] + (i - b_off[lo])];
+                    if (!tri) {
+                        drop(e);
+                    } else {
+                        unsigned int* word = (unsigned int*)(tdead + (e & ~3));
+                        const unsigned int bit = 1u << (8 * (e & 3));
+                        if (atomicOr(word, bit) & bit) continue;      // died with another vertex
+                        const int32_t va = ta[e], vb = tb[e], vc = tc[e];
+                        if (va != xv) drop(va);
+                        if (vb != xv) drop(vb);
+                        if (vc != xv) drop(vc);
+                    }
+                }
+                __syncthreads();
+            }
+            nf = sc[0];
+            __syncthreads();
+            int32_t* t = cf;
+            cf = nx;
+            nx = t;
+        }
+        k = k + 1;
+    }
+}
+
 // Whole peeling loop in one cooperative launch (peeling by levels).  A level k
 // starts with a scan of the live-vertex list: vertices with count <= k are
 // peeled (core k) into the frontier, the others go to the other list, and the
@@ -256,12 +403,12 @@ constexpr int PEEL_CHUNK = 128;     // otherwise a warp removes each chunk of th
 // frontier and collect the vertices that fall to k: a lane removes a vertex
 // with few incidences itself, and the incidences of the others are cut into
 // chunks that all warps share, so a hub does not hold up the round.  Once the
-// live list is down to `solo` vertices, block 0 finishes alone with
-// block-wide barriers, which cost far less than grid-wide ones over the many
-// small levels of the dense tail.
+// live list is down to `solo` (at most PEEL_SOLO) vertices, the grid stops and
+// peel_solo_kernel finishes in one block: block barriers cost far less than
+// grid barriers over the many small levels of the dense tail.
 // ctrl: [0..1] frontier counts, [2] smallest kept count, [3] error (bound hit),
 // [4..5] live-list counts, [6..7] steps and last level (reported at the end),
-// [8] chunk count; they move to shared memory when block 0 goes on alone.  Every
+// [8] chunk count, [9..12] the hand-over (live list, level, steps, flag).  Every
 // thread follows the same k and the same branches: the counters are read right
 // after a barrier.
 __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int64_t* rowptr, const int32_t* col,
@@ -270,24 +417,15 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
                                                             uint8_t* tdead, uint8_t* alive, int32_t* deg,
                                                             int64_t* core, int32_t* F0, int32_t* F1, int32_t* A0,
                                                             int32_t* A1, int32_t* qv, int64_t* qs,
-                                                            unsigned long long* gctrl, int64_t max_steps,
+                                                            unsigned long long* ctrl, int64_t max_steps,
                                                             int64_t solo) {
     cg::grid_group grid = cg::this_grid();
-    // control words: global while the grid works, in shared memory once block 0 is alone
-    __shared__ unsigned long long sctrl[9];
-    unsigned long long* ctrl = gctrl;
-    bool whole = true;                       // all blocks take part (grid barriers)
-    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    int64_t warp = tid >> 5, nwarps = nthreads >> 5;
-    auto barrier = [&]() {
-        if (whole) grid.sync();
-        else __syncthreads();
-    };
-    auto rd = [&](int i) -> unsigned long long {
-        return whole ? __ldcg(gctrl + i) : static_cast<volatile unsigned long long*>(sctrl)[i];
-    };
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    auto barrier = [&]() { grid.sync(); };
+    auto rd = [&](int i) -> unsigned long long { return __ldcg(ctrl + i); };
     const int64_t* ptr = tri ? vptr : rowptr;
     const int32_t* adj = tri ? vtri : col;
     auto F = [&](int i) { return i ? F1 : F0; };
@@ -296,20 +434,19 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
     int64_t k = 0, steps = 0;
     for (;;) {
         if (++steps > max_steps) {
-            if (tid == 0) gctrl[3] = 1;
+            if (tid == 0) ctrl[3] = 1;
             return;
         }
         const int64_t na = (int64_t)rd(4 + a);
-        if (whole && na <= solo) {
-            if (blockIdx.x != 0) return;
-            whole = false;
-            tid = threadIdx.x;
-            nthreads = blockDim.x;
-            warp = tid >> 5;
-            nwarps = nthreads >> 5;
-            if (threadIdx.x < 9) sctrl[threadIdx.x] = __ldcg(gctrl + threadIdx.x);
-            __syncthreads();
-            ctrl = sctrl;
+        if (na <= solo) {
+            // peel_solo_kernel, launched next, finishes in one block
+            if (tid == 0) {
+                ctrl[9] = (unsigned long long)a;
+                ctrl[10] = (unsigned long long)k;
+                ctrl[11] = (unsigned long long)(steps - 1);
+                ctrl[12] = 1;
+            }
+            return;
         }
         // level scan, warp by warp: one atomic per warp for each list and for the minimum
         for (int64_t base = tid - lane; base < na; base += nthreads) {
@@ -357,8 +494,8 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         if (f == 0) {
             if (kept == 0) {
                 if (tid == 0) {
-                    gctrl[6] = (unsigned long long)steps;
-                    gctrl[7] = (unsigned long long)k;
+                    ctrl[6] = (unsigned long long)steps;
+                    ctrl[7] = (unsigned long long)k;
                 }
                 return;
             }
@@ -369,7 +506,7 @@ __global__ void __launch_bounds__(1024, 1) peel_coop_kernel(bool tri, const int6
         // frontier rounds at level k
         while (f > 0) {
             if (++steps > max_steps) {
-                if (tid == 0) gctrl[3] = 1;
+                if (tid == 0) ctrl[3] = 1;
                 return;
             }
             int32_t* fr = F(cur);
@@ -451,11 +588,6 @@ __global__ void alive_list_kernel(const uint8_t* alive, int32_t nact, int32_t* l
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nact; x += stride)
         if (alive[x]) list[agg_slot(cnt)] = (int32_t)x;
-}
-
-__global__ void set_i64_kernel(int64_t* p, int32_t from, int32_t to, int64_t v) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = from + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < to; x += stride) p[x] = v;
 }
 
 }  // namespace
@@ -585,8 +717,8 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_CUDA(cudaStreamSynchronize(s));
     if (remaining == 0) return;
     // one cooperative launch runs every level; the grid must be resident at once
-    DevBuf<unsigned long long> ctrl(9, s);
-    unsigned long long hctrl[9] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    DevBuf<unsigned long long> ctrl(13, s);
+    unsigned long long hctrl[13] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     LDS_CUDA(cudaMemcpyAsync(ctrl.get(), hctrl, sizeof(hctrl), cudaMemcpyHostToDevice, s));
     DevBuf<int32_t> F1(nact, s), A0(nact, s), A1(nact, s);
     // chunk queue: at most one chunk per vertex plus one per PEEL_CHUNK incidences
@@ -599,10 +731,14 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     const int pblk = 1024;
     int per_sm = 0;
     LDS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_coop_kernel, pblk, 0));
+    LDS_CUDA(cudaFuncSetAttribute(peel_solo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PEEL_SOLO_SMEM));
     LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "core numbers: peeling kernel cannot be resident");
     int grid = std::max(1, std::min(num_sms(), (int)((nact + pblk - 1) / pblk)));
     int64_t max_steps = 4 * (int64_t)nact + 64;
-    int64_t solo = 16384;
+    int64_t solo = PEEL_SOLO;
+    DevBuf<int32_t> slotb(nact, s);
+    LDS_CUDA(cudaMemsetAsync(slotb.get(), 0xff, (size_t)nact * sizeof(int32_t), s));
+    int32_t* slp = slotb.get();
     bool trib = tri;
     const int64_t* rp = g->rowptr.get();
     const int32_t* cl = g->col.get();
@@ -633,6 +769,8 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
         LDS_CUDA(cudaEventRecord(e0, s));
     }
     LDS_CUDA(cudaLaunchCooperativeKernel((void*)peel_coop_kernel, dim3(grid), dim3(pblk), args, 0, s));
+    LDS_LAUNCH(peel_solo_kernel, 1, PEEL_SOLO_T, PEEL_SOLO_SMEM, s, trib, tri ? tvp : g->rowptr.get(),
+               tri ? tvi : g->col.get(), pa, pb, pc, td, al, dg, core_int, a0, a1, slp, ct, max_steps);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (verbose) LDS_CUDA(cudaEventRecord(e1, s));
     LDS_CUDA(cudaMemcpyAsync(hctrl, ctrl.get(), sizeof(hctrl), cudaMemcpyDeviceToHost, s));

@@ -109,6 +109,7 @@ def load():
     _sig(lib, "lds_launch_count", i64, [])
     _sig(lib, "lds_set_fw_variant", ctypes.c_int, [i32])
     _sig(lib, "lds_set_flow_variant", ctypes.c_int, [i32])
+    _sig(lib, "lds_set_extract_variant", ctypes.c_int, [i32])
     _sig(lib, "lds_pattern_max_flow", ctypes.c_int, [i32, i32, P, P, i64, i64, ctypes.POINTER(i64), P])
     _sig(lib, "lds_prune", ctypes.c_int, [P, ctypes.c_int, P, P, P, P, P])
     _sig(lib, "lds_topk", ctypes.c_int, [P, i32, ctypes.c_int, i32, ctypes.c_int,
@@ -173,6 +174,11 @@ def set_fw_variant(variant: int):
 def set_flow_variant(variant: int):
     """0: automatic; 1: pattern-node push-relabel; 2: vertex-node phases."""
     _check(load().lds_set_flow_variant(int(variant)))
+
+
+def set_extract_variant(variant: int):
+    """0: automatic; 1: the large-graph ExtractSG walk (device chains) at every size."""
+    _check(load().lds_set_extract_variant(int(variant)))
 
 
 def launch_count() -> int:

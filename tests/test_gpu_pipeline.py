@@ -40,8 +40,17 @@ def _ir(n, u, v, tris=None):
     return ({x: Fraction(int(core[x])) for x in range(n)}, {x: Fraction(int(core[x]), div) for x in range(n)})
 
 
+@pytest.fixture(params=[0, 1], ids=["walk_by_size", "walk_device_chains"])
+def sg_variant(lds, request):
+    # 1 runs the large-graph walk (host loop, each chain of merged candidates in
+    # one device launch) on these small graphs too
+    lds.set_extract_variant(request.param)
+    yield request.param
+    lds.set_extract_variant(0)
+
+
 @pytest.mark.parametrize("N", [2, 30, 250])
-def test_extract_sg_edge_matches_oracle(lds, N):
+def test_extract_sg_edge_matches_oracle(lds, N, sg_variant):
     for n, u, v in _graphs():
         with lds.Graph(n, u, v) as g:
             g.fw(N, precision="exact", want=())
@@ -58,7 +67,7 @@ def test_extract_sg_edge_matches_oracle(lds, N):
 
 
 @pytest.mark.parametrize("N", [2, 40])
-def test_extract_sg_triangle_matches_oracle(lds, N):
+def test_extract_sg_triangle_matches_oracle(lds, N, sg_variant):
     for n, u, v in _graphs():
         tris = ograph.triangles(n, u, v)
         with lds.Graph(n, u, v) as g:
@@ -317,3 +326,19 @@ def test_compact_numbers_many_levels_match_oracle(lds, triangle):
     with lds.Graph(n, a, b) as g:
         got = _as_lists(g.topk(6, "triangle" if triangle else "edge", 100))
     assert got == [(d, c) for d, c in truth[:6]]
+
+
+def test_topk_device_chain_walk_matches_definition(lds):
+    # the whole driver with the large-graph ExtractSG walk, against the oracle's
+    # decomposition, on graphs whose early rounds merge candidates
+    from oracle import decomp
+    lds.set_extract_variant(1)
+    try:
+        for n, u, v in _graphs()[:3]:
+            cu, cv = ograph.canonical_edges(n, u, v)
+            truth = decomp.lds_exact(n, cu, cv)
+            with lds.Graph(n, u, v) as g:
+                for N in (3, 40):
+                    assert _as_lists(g.topk(4, "edge", N)) == [(d, c) for d, c in truth[:4]], (n, N)
+    finally:
+        lds.set_extract_variant(0)
