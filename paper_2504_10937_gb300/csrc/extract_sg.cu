@@ -450,11 +450,36 @@ __device__ __forceinline__ void chain_track(bool tri, int64_t p, int64_t r, cons
     }
 }
 
+// exclusive scan of one int64 per thread over a block of 1024 threads; returns the total
+__device__ __forceinline__ int64_t cw_block_scan(int64_t v, int64_t* out, int64_t* wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    int64_t inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    out[tid] = inc - v + (wid ? wsum[wid - 1] : 0);
+    const int64_t total = wsum[31];
+    __syncthreads();
+    return total;
+}
+
 // Chain state kept in device memory between launches (cws, 8 words): [0] min X,
 // [1] max S (running), [2] listed dirty chunks, [3] end b of S, [4] next
 // candidate, [5] 1 when that candidate's patterns are already applied, [6] steps,
 // [7] 1 once the chunk maxima of Z are set up.
-constexpr int64_t CW_HEAVY = 65536;   // a step with more incidences runs grid-wide
+constexpr int64_t CW_HEAVY = 16384;   // a step with more incidences runs grid-wide
 
 // One chain of merged candidates with start a (S = [a, cb[k]] for k = cws[4],
 // cws[4] + 1, ...), in one CTA: stops at the first candidate whose two checks
@@ -473,6 +498,7 @@ __global__ void __launch_bounds__(1024) chain_walk_kernel(
     __shared__ unsigned long long red[2][32];
     __shared__ long long s_cnt;
     __shared__ int32_t s_nd, s_done;
+    __shared__ int64_t s_off[1024], s_wsum[32];
     const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = bd >> 5;
     const int64_t nchunks = ((int64_t)n + CW_CHUNK - 1) / CW_CHUNK;
     const int64_t nsuper = (nchunks + CW_SUPER - 1) / CW_SUPER;
@@ -530,13 +556,28 @@ __global__ void __launch_bounds__(1024) chain_walk_kernel(
                                     tb, tc, W, Dn, R, delta, &s_minX, &s_maxS, cZ, sZ, dirty, dlist, &s_nd);
                 }
             } else {
-                for (int64_t p = b0 + 1 + wid; p <= b1; p += nw) {
-                    const int32_t x = order[p];
-                    if (x >= nact) continue;
-                    const int64_t deg = tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
-                    for (int64_t r = lane; r < deg; r += 32)
-                        chain_track(tri, p, r, order, pos, a, b0, b1, rowptr, col, slot_edge, eu, vt_ptr, vt_idx, ta,
-                                    tb, tc, W, Dn, R, delta, &s_minX, &s_maxS, cZ, sZ, dirty, dlist, &s_nd);
+                // several positions: their incidences spread evenly over the block, in
+                // batches of one position per thread (scan of the incidence counts)
+                for (int64_t base = b0 + 1; base <= b1; base += bd) {
+                    const int64_t p = base + tid;
+                    int64_t d = 0;
+                    if (p <= b1) {
+                        const int32_t x = order[p];
+                        if (x < nact) d = tri ? vt_ptr[x + 1] - vt_ptr[x] : rowptr[x + 1] - rowptr[x];
+                    }
+                    const int64_t total = cw_block_scan(d, s_off, s_wsum);
+                    const int32_t cnt = (int32_t)min((int64_t)bd, b1 - base + 1);
+                    for (int64_t i = tid; i < total; i += bd) {
+                        int32_t lo = 0, hi = cnt;            // last position with offset <= i
+                        while (hi - lo > 1) {
+                            const int32_t mid = (lo + hi) >> 1;
+                            if (s_off[mid] <= i) lo = mid; else hi = mid;
+                        }
+                        chain_track(tri, base + lo, i - s_off[lo], order, pos, a, b0, b1, rowptr, col, slot_edge, eu,
+                                    vt_ptr, vt_idx, ta, tb, tc, W, Dn, R, delta, &s_minX, &s_maxS, cZ, sZ, dirty, dlist,
+                                    &s_nd);
+                    }
+                    __syncthreads();
                 }
             }
         }

@@ -735,7 +735,10 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_REQUIRE(per_sm > 0, LDS_ECUDA, "core numbers: peeling kernel cannot be resident");
     int grid = std::max(1, std::min(num_sms(), (int)((nact + pblk - 1) / pblk)));
     int64_t max_steps = 4 * (int64_t)nact + 64;
-    int64_t solo = PEEL_SOLO;
+    // the one-block tail only for edges: a triangle tail's incidences (hub
+    // triangles) keep the whole grid busy (R-MAT 20: 3.1 s instead of 5.9 s per
+    // LTDS query with the tail in one block)
+    int64_t solo = tri ? 0 : PEEL_SOLO;
     DevBuf<int32_t> slotb(nact, s);
     LDS_CUDA(cudaMemsetAsync(slotb.get(), 0xff, (size_t)nact * sizeof(int32_t), s));
     int32_t* slp = slotb.get();
