@@ -41,12 +41,16 @@ UNIT = "edge-updates/s"
 METRIC_TRI = "FW triangle-updates/s"
 UNIT_TRI = "triangle-updates/s"
 
-# DRAM bytes (read + write) of one launch of the FW pass kernel on this workload,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# DRAM bytes (read + write) per iteration of the FW kernel on this workload, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # the kernel, the arithmetic and a digest of the source file the kernel was built
 # from at capture time.  A kernel whose source changed since has no matching entry
 # and reports null.
-PASS_TRAFFIC = {}
+PASS_TRAFFIC = {
+    # one 20-iteration launch on the 1M-vertex workload (64,239,872 B read + 4,828,928 B
+    # written, the cold first read of the view included), per iteration
+    ("fw_coop32_kernel", "exact", "1df8d6eea5f0f836"): 3453440,
+}
 PASS_SOURCE = {"fw_opass32_kernel": "paper_2504_10937_gb300/csrc/fw_oriented.cu",
                "fw_coop32_kernel": "paper_2504_10937_gb300/csrc/fw_oriented.cu",
                "fw_tri_pass_kernel": "paper_2504_10937_gb300/csrc/fw.cu"}
