@@ -375,6 +375,8 @@ void set_stream(lds_graph* g, cudaStream_t s) {
     g->tc.s = s;
     g->vt_ptr.s = s;
     g->vt_idx.s = s;
+    g->core_all[0].s = s;
+    g->core_all[1].s = s;
     g->fwv_perm.s = s;
     g->fwv_pos.s = s;
     g->fwv_col.s = s;

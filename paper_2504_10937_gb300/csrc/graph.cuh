@@ -31,6 +31,9 @@ struct lds_graph {
     // vertex -> triangle incidence (lazy): triangles of x at vt_idx[vt_ptr[x] .. vt_ptr[x+1]), ascending
     lds::DevBuf<int64_t> vt_ptr;      // [nact + 1]
     lds::DevBuf<int32_t> vt_idx;      // [3 |T|]
+    // core numbers of the whole graph (lazy), [0] edge, [1] triangle: a peel with
+    // every vertex alive is the same every time the handle asks
+    lds::DevBuf<int64_t> core_all[2];
 
     // FW view: vertices relabelled by (degree descending, id ascending); every
     // edge stored once, in the row of its lower-ranked endpoint, pointing to the

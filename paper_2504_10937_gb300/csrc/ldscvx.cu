@@ -782,15 +782,16 @@ void Driver::run() {
                 fprintf(stderr, "[lds_topk]   component %d (|P|=%lld): not densest %.1f ms\n", csize, (long long)npat,
                         std::chrono::duration<double, std::milli>(tv2 - tv1).count());
             tm.verify += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tv1).count();
-            // refine on G[comp]
+            // refine on G[comp] (one handle for every retry: its whole-graph core
+            // numbers are peeled once)
             int32_t n_try = N;
+            auto tsub = std::chrono::steady_clock::now();
+            lds_graph* h = subgraph(G, comp, csize, sc);
+            struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
+            tm.sub += ms_since(tsub);
             while (true) {
                 ++stats.refined;
                 auto ts = std::chrono::steady_clock::now();
-                lds_graph* h = subgraph(G, comp, csize, sc);
-                struct Free { lds_graph* h; ~Free() { lds_free(h); } } fr{h};
-                tm.sub += ms_since(ts);
-                ts = std::chrono::steady_clock::now();
                 Bounds bs;
                 init_bounds(h, bs);
                 LDS_CUDA(cudaStreamSynchronize(s));

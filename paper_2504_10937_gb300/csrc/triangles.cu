@@ -716,6 +716,13 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
     LDS_CUDA(cudaMemcpyAsync(&remaining, nalive.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LDS_CUDA(cudaStreamSynchronize(s));
     if (remaining == 0) return;
+    // every vertex alive: the whole graph's core numbers, peeled once per handle
+    DevBuf<int64_t>& whole = g->core_all[tri ? 1 : 0];
+    const bool all_alive = remaining == nact;
+    if (all_alive && whole.p) {
+        LDS_CUDA(cudaMemcpyAsync(core_int, whole.get(), (size_t)nact * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        return;
+    }
     // one cooperative launch runs every level; the grid must be resident at once
     DevBuf<unsigned long long> ctrl(13, s);
     unsigned long long hctrl[13] = {0ull, 0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
@@ -787,6 +794,10 @@ static void core_numbers_internal(lds_graph* g, bool tri, int64_t* core_int, con
         cudaEventDestroy(e1);
     }
     LDS_REQUIRE(hctrl[3] == 0, LDS_ETIMEOUT, "core numbers: peeling hit its iteration bound");
+    if (all_alive) {
+        whole.alloc(nact, s);
+        LDS_CUDA(cudaMemcpyAsync(whole.get(), core_int, (size_t)nact * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    }
 }
 
 void core_numbers(lds_graph* g, bool tri, int64_t* core_int_out, const uint8_t* init_alive) {
