@@ -25,7 +25,10 @@ Readings of the paper:
   touches S, has an X vertex and no Z vertex gives all its weight to its
   lowest-r S vertex; a triangle inside S is unchanged.
 * A candidate that fails is merged with the next one (Alg. 2, loop); a trailing
-  remainder that never passes gives no bounds.
+  remainder that never passes gives no bounds.  For a fixed start, growing the
+  segment only lowers the modified loads of X and only raises max_S r', so
+  after a failure on the X side no longer merge can pass: the walk stops there
+  (exhaustive=True walks on; the pins check that both give the same groups).
 
 Pins (tests/test_oracle_stages.py): on the reconstructed Fig. 1 graph at
 the optimum the groups are S1, S2, S3, {g, h, i} with Table 2's values; the
@@ -59,19 +62,23 @@ def cut_points(prefix_counts):
     return sorted(cuts)
 
 
-def _groups_from_checks(nv, cuts, check):
+def _groups_from_checks(nv, cuts, check, exhaustive=False):
     groups = []
     start = 0
     for c in cuts:
         b = c - 1
-        ok, lo, hi = check(start, b)
+        ok, lo, hi, xok = check(start, b)
         if ok:
             groups.append((start, b, lo, hi))
             start = b + 1
+        elif not xok and not exhaustive:
+            # the X side only gets worse as this start's segment grows: no later
+            # candidate passes, the rest is the remainder
+            break
     return groups, start
 
 
-def extract_sg_edge(vertices, u, v, W, Dn: int, ub, lb):
+def extract_sg_edge(vertices, u, v, W, Dn: int, ub, lb, exhaustive=False):
     """Alg. 2 for edge density on G' = (vertices, edges u < v).
 
     W[e] = Dn * alpha_{u[e], v[e]}.  ub / lb map vertex -> Fraction and are
@@ -117,16 +124,16 @@ def extract_sg_edge(vertices, u, v, W, Dn: int, ub, lb):
             Rm[x] = val
         lo = min(Rm.values())
         hi = max(Rm.values())
-        ok = True
+        xok = zok = True
         if a > 0:
             min_x = min([R[order[a - 1]]] + list(x_adj.values()))
-            ok &= min_x > hi
+            xok = min_x > hi
         if b < nv - 1:
             max_z = max([R[order[b + 1]]] + list(z_adj.values()))
-            ok &= max_z < lo
-        return ok, lo, hi
+            zok = max_z < lo
+        return xok and zok, lo, hi, xok
 
-    groups, start = _groups_from_checks(nv, cuts, check)
+    groups, start = _groups_from_checks(nv, cuts, check, exhaustive)
     ub = dict(ub)
     lb = dict(lb)
     out_groups, intervals = [], []
@@ -141,7 +148,7 @@ def extract_sg_edge(vertices, u, v, W, Dn: int, ub, lb):
                 intervals=intervals, remainder=order[start:], ub=ub, lb=lb, R=R)
 
 
-def extract_sg_tri(vertices, tris, W, Dn3: int, ub, lb):
+def extract_sg_tri(vertices, tris, W, Dn3: int, ub, lb, exhaustive=False):
     """Alg. 2 adapted to triangle density (Def. 12, reading in the module
     header).  tris (|T|, 3) lists the triangles of G'; W[t][k] = Dn3 *
     alpha_{tris[t][k], t} with Dn3 = 3 D_N.  Same return keys as
@@ -190,16 +197,16 @@ def extract_sg_tri(vertices, tris, W, Dn3: int, ub, lb):
         Rm = {x: R[x] + delta.get(x, 0) for x in S}
         lo = min(Rm.values())
         hi = max(Rm.values())
-        ok = True
+        xok = zok = True
         if a > 0:
             xv = [R[y] + d for y, d in delta.items() if pos[y] < a]
-            ok &= min([R[order[a - 1]]] + xv) > hi
+            xok = min([R[order[a - 1]]] + xv) > hi
         if b < nv - 1:
             zv = [R[y] + d for y, d in delta.items() if pos[y] > b]
-            ok &= max([R[order[b + 1]]] + zv) < lo
-        return ok, lo, hi
+            zok = max([R[order[b + 1]]] + zv) < lo
+        return xok and zok, lo, hi, xok
 
-    groups, start = _groups_from_checks(nv, cuts, check)
+    groups, start = _groups_from_checks(nv, cuts, check, exhaustive)
     ub = dict(ub)
     lb = dict(lb)
     out_groups, intervals = [], []

@@ -77,6 +77,28 @@ def test_triangle_bounds_contain_exact_phi(seed):
             assert res["lb"][x] <= phi[x] <= res["ub"][x]
 
 
+@pytest.mark.parametrize("seed", range(10))
+def test_walk_stop_at_x_failure_keeps_groups(seed):
+    # growing a segment only lowers X's modified loads and raises max_S r', so the
+    # walk that stops at the first X-side failure finds the groups of the walk
+    # that tries every later candidate (edges and triangles, rough and refined FW)
+    n, u, v, _ = random_planted(36, 0.09, (7, 6), (0.9, 0.75), seed=5600 + seed)
+    tris = graph.triangles(n, u, v)
+    core = graph.tr_core_numbers(n, tris)
+    for N in (2, 5, 40):
+        R, W, Dn, _ = fw.fw_edge_exact(n, u, v, N)
+        ub, lb = _ir_bounds(n, u, v)
+        a = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb)
+        b = extract_sg.extract_sg_edge(range(n), u, v, W, Dn, ub, lb, exhaustive=True)
+        assert (a["groups"], a["intervals"], a["ub"], a["lb"]) == (b["groups"], b["intervals"], b["ub"], b["lb"])
+        R, W3, Dn3, _ = fw.fw_tri_exact(n, tris, N)
+        ubt = {x: Fraction(int(core[x])) for x in range(n)}
+        lbt = {x: Fraction(int(core[x]), 3) for x in range(n)}
+        a = extract_sg.extract_sg_tri(range(n), tris, W3, Dn3, ubt, lbt)
+        b = extract_sg.extract_sg_tri(range(n), tris, W3, Dn3, ubt, lbt, exhaustive=True)
+        assert (a["groups"], a["intervals"], a["ub"], a["lb"]) == (b["groups"], b["intervals"], b["ub"], b["lb"])
+
+
 # ---------------------------------------------------------------- Pruning
 
 def test_fig1_pruning_example():
