@@ -146,9 +146,9 @@ def is_connected(vertices, adj):
 
 def core_numbers(n: int, u, v, vertices=None):
     """Core number of every vertex of G[vertices] (Def. 6) by peeling:
-    repeatedly delete a vertex of minimum remaining degree; a vertex's core
-    number is the largest minimum degree seen up to its deletion.  Vertices
-    outside ``vertices`` get -1."""
+    repeatedly delete a vertex of minimum remaining degree (any one of them);
+    a vertex's core number is the largest minimum degree seen up to its
+    deletion.  Vertices outside ``vertices`` get -1."""
     alive = set(range(n)) if vertices is None else set(int(x) for x in vertices)
     adj = adjacency_sets(n, u, v)
     deg = {x: len(adj[x] & alive) for x in alive}
@@ -159,10 +159,14 @@ def core_numbers(n: int, u, v, vertices=None):
     for x, d in deg.items():
         buckets.setdefault(d, set()).add(x)
     remaining = set(alive)
+    lo = 0                               # no nonempty bucket below lo
     while remaining:
-        d = min(b for b, s in buckets.items() if s)
-        x = min(buckets[d])
-        buckets[d].discard(x)
+        d = lo
+        while not buckets.get(d):
+            d += 1
+        # which vertex of minimum degree goes first does not change any core number
+        x = buckets[d].pop()
+        lo = d
         k = max(k, d)
         core[x] = k
         remaining.discard(x)
@@ -172,6 +176,7 @@ def core_numbers(n: int, u, v, vertices=None):
                 buckets[dy].discard(y)
                 deg[y] = dy - 1
                 buckets.setdefault(dy - 1, set()).add(y)
+                lo = min(lo, dy - 1)
     return core
 
 
@@ -194,10 +199,14 @@ def tr_core_numbers(n: int, tris, vertices=None):
         buckets.setdefault(d, set()).add(x)
     remaining = set(alive)
     k = 0
+    lo = 0                               # no nonempty bucket below lo
     while remaining:
-        d = min(b for b, s in buckets.items() if s)
-        x = min(buckets[d])
-        buckets[d].discard(x)
+        d = lo
+        while not buckets.get(d):
+            d += 1
+        # which vertex of minimum count goes first does not change any tr-core number
+        x = buckets[d].pop()
+        lo = d
         k = max(k, d)
         core[x] = k
         remaining.discard(x)
@@ -211,6 +220,7 @@ def tr_core_numbers(n: int, tris, vertices=None):
                     buckets[dw].discard(w)
                     tcount[w] = dw - 1
                     buckets.setdefault(dw - 1, set()).add(w)
+                    lo = min(lo, dw - 1)
     return core
 
 
