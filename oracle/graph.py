@@ -78,12 +78,21 @@ def degrees(n: int, u, v):
     return d
 
 
+def _member_mask(S, *arrays):
+    """Boolean membership table over ids 0 .. (largest id seen) for the set S."""
+    Sa = np.asarray(list(S) if not isinstance(S, np.ndarray) else S, dtype=np.int64)
+    top = max([int(a.max()) for a in arrays if a.size] + [int(Sa.max()) if Sa.size else -1] + [0])
+    mask = np.zeros(top + 1, dtype=bool)
+    mask[Sa] = True
+    return mask
+
+
 def induced_edges(u, v, S):
     """E(S) as a pair of arrays (u < v kept, order kept)."""
-    inS = set(int(x) for x in S)
-    keep = [i for i, (a, b) in enumerate(zip(np.asarray(u).tolist(), np.asarray(v).tolist()))
-            if a in inS and b in inS]
-    return np.asarray(u)[keep], np.asarray(v)[keep]
+    ua, va = np.asarray(u), np.asarray(v)
+    mask = _member_mask(S, ua.astype(np.int64), va.astype(np.int64))
+    keep = mask[ua.astype(np.int64)] & mask[va.astype(np.int64)]
+    return ua[keep], va[keep]
 
 
 def triangles(n: int, u, v):
@@ -101,9 +110,12 @@ def triangles(n: int, u, v):
 
 
 def induced_triangles(tris, S):
-    inS = set(int(x) for x in S)
-    keep = [i for i, t in enumerate(np.asarray(tris).tolist()) if t[0] in inS and t[1] in inS and t[2] in inS]
-    return np.asarray(tris).reshape(-1, 3)[keep]
+    """The triangles (rows a, b, c) with all three vertices in S, order kept."""
+    t = np.asarray(tris).reshape(-1, 3)
+    ti = t.astype(np.int64)
+    mask = _member_mask(S, ti)
+    keep = mask[ti[:, 0]] & mask[ti[:, 1]] & mask[ti[:, 2]]
+    return t[keep]
 
 
 def triangle_degrees(n: int, tris):
