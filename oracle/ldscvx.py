@@ -128,8 +128,13 @@ def _count_patterns(g: _Graph, comp):
 
 
 def _patterns(g: _Graph, comp):
+    """The patterns of G[comp]: its triangles, or its edges (u, v), u < v."""
     if g.triangle:
         return [tuple(t) for t in induced_triangles(g.tris, comp).tolist()]
+    if len(comp) <= 4096:
+        # a small set: from its members' neighbour lists, not a scan of every edge
+        cs = set(int(x) for x in comp)
+        return [(x, y) for x in sorted(cs) for y in g.adj[x] if y > x and y in cs]
     eu, ev = induced_edges(g.u, g.v, comp)
     return list(zip(eu.tolist(), ev.tolist()))
 
