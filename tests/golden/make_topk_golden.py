@@ -4,7 +4,7 @@ the CPU oracle (oracle.ldscvx.topk, exact arithmetic) on them.
 Only the oracle and the seeded input generators are used: no value comes from
 the CUDA library.  Usage (from the repository root):
 
-    python tests/golden/make_topk_golden.py chung_lu_1m     # about an hour on one core
+    python tests/golden/make_topk_golden.py chung_lu_1m     # about 10 minutes on one core
     python tests/golden/make_topk_golden.py rmat12
 
 Each output file holds one line per set, densest first, in the format the
